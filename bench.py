@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark: family scores per second of the all-families Givens walk.
+
+One step = one call of score_all_families on the m=26, n=5000 SEM workload
+(two near-collinear columns): CholeskyQR2 R0 in FP64, the sub-walk roots and
+the Givens walk writing all m*2^(m-1) = 872,415,232 BIC scores to HBM.  The
+headline is the FP32 walk; the plain FP64 walk is timed beside it.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank scores its
+own dataset (seed + rank): weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "family scores/sec (all m*2^(m-1)) at m=26, FP32 vs plain FP64, on 1 GB300"
+UNIT = "family scores/s"
+FALLBACK_HBM_GBS = 6800.0
+WALK_SOURCES = ["paper_1901_07643_gb300/csrc/walk.cuh", "paper_1901_07643_gb300/csrc/walk_inst.cu",
+                "paper_1901_07643_gb300/csrc/gbn_internal.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk_traffic.json")
+LAUNCHES_PER_STEP = 7  # colsum, gram x2, cholesky x2, roots, walk
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="m26", choices=["m26", "m20", "m10"])
+    ap.add_argument("--q", type=int, default=0)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def _workload(name):
+    from paper_1901_07643_gb300 import synthetic
+    return {"m26": synthetic.LARGE_M26, "m20": synthetic.MEDIUM_M20,
+            "m10": synthetic.SMALL_M10}[name]
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    for p in WALK_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _traffic(workload_name):
+    """Per-launch DRAM bytes of the walk kernel from the committed ncu summary, if current."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_hash") != _source_hash() or d.get("workload") != workload_name:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _gpu_id(dev_index):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev_index).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[dev_index] if vis else str(dev_index)
+
+
+def _cpu_baseline(X, n, m, seconds):
+    """Oracle (direct FP64 Householder per family) on a bounded sample of the workload."""
+    import oracle
+    cores = _cores()
+    rng = np.random.default_rng(12345)
+
+    def sample(count):
+        child = rng.integers(0, m, count).astype(np.int32)
+        mask = np.array([int(rng.integers(0, 1 << m)) & ~(1 << int(c)) for c in child], np.uint64)
+        return child, mask
+
+    c, k = sample(max(cores * 4, 32))
+    t0 = time.perf_counter()
+    oracle.scores_sampled(X, c, k, nthreads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    count = int(min(2_000_000, max(len(c), len(c) * seconds / dt)))
+    c, k = sample(count)
+    t0 = time.perf_counter()
+    oracle.scores_sampled(X, c, k, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": count / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{count} random families of the m={m}, n={n} workload, direct FP64 "
+                      f"Householder QR per family, OpenMP over families; {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_1901_07643_gb300 import synthetic
+    import oracle
+    w = _workload(args.workload)
+    X = synthetic.workload_sample(w)
+    cores = _cores()
+    rng = np.random.default_rng(777)
+    fam_total = w.m << (w.m - 1)
+
+    def step(count):
+        child = rng.integers(0, w.m, count).astype(np.int32)
+        mask = np.array([int(rng.integers(0, 1 << w.m)) & ~(1 << int(c)) for c in child], np.uint64)
+        t0 = time.perf_counter()
+        oracle.scores_sampled(X, child, mask, nthreads=cores)
+        return time.perf_counter() - t0
+
+    dt = step(max(4 * cores, 32))
+    per_step = int(max(4 * cores, 32) * min(8.0, 160.0 / max(1, args.steps + args.warmup)) /
+                   max(dt, 1e-3))
+    per_step = max(per_step, cores)
+    for _ in range(args.warmup):
+        step(per_step)
+    times = [step(per_step) for _ in range(args.steps)]
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "m": w.m, "n": w.n, "families": fam_total,
+                   "step": f"{per_step} sampled families (bounded sample of the workload)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} random families per step, direct FP64 "
+                                   "Householder QR per family"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _time_steps(fn, steps, flush, stream):
+    """Per-step CUDA-event durations (ms) and walk-stage durations (ms)."""
+    import torch
+    step_ms, walk_ms = [], []
+    pairs = []
+    for _ in range(steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        fn(ev)
+        pairs.append(ev)
+    torch.cuda.synchronize()
+    for ev in pairs:
+        step_ms.append(ev[0].elapsed_time(ev[3]))
+        walk_ms.append(ev[2].elapsed_time(ev[3]))
+    return step_ms, walk_ms
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1901_07643_gb300 import binding, synthetic
+
+    rank, world, local = _dist()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = _workload(args.workload)
+    X = synthetic.sem_sample(w.m, w.n, w.edge_p, w.seed + rank, w.collinear)
+    fam = w.m << (w.m - 1)
+    stream = torch.cuda.current_stream(dev)
+    Xd = torch.from_numpy(X).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def make(precision):
+        q = args.q if (args.q and (precision == 0 or args.q <= 7)) else 0
+        out = torch.empty(fam, dtype=torch.float64 if precision else torch.float32, device=dev)
+        ws = torch.empty(binding.workspace_size(w.n, w.m, precision, q), dtype=torch.uint8,
+                         device=dev)
+
+        def fn(ev):
+            binding.score_all_families(Xd, out, precision=precision, q=q, workspace=ws,
+                                       stage_events=ev, check=False)
+        return fn, out, ws, q
+
+    fn32, out32, ws32, q32 = make(0)
+    for _ in range(max(args.warmup, 0)):
+        fn32([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+    binding.score_all_families(Xd, out32, q=q32, workspace=ws32, check=True)  # status check
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(out32).all()), "non-finite scores"
+
+    sampler = ClockSampler(_gpu_id(local)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, walk_ms = _time_steps(fn32, args.steps, flush, stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * fam * args.steps / (total_ms / 1e3)
+    walk_mean = statistics.mean(walk_ms)
+    del out32, ws32
+    torch.cuda.empty_cache()
+
+    fp64 = None
+    if not args.skip_fp64:
+        fn64, out64, ws64, q64 = make(1)
+        for _ in range(max(args.warmup, 1)):
+            fn64([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+        k64 = max(3, args.steps // 2)
+        s64, w64 = _time_steps(fn64, k64, flush, stream)
+        fp64 = {"value": fam * k64 / (sum(s64) / 1e3), "ms_per_step": statistics.mean(s64),
+                "walk_ms": statistics.mean(w64), "q": binding.auto_q(w.m, 1) if not q64 else q64,
+                "dtype": "f64", "steps": k64}
+        del out64, ws64
+        torch.cuda.empty_cache()
+
+    e2e = None
+    if not args.skip_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        outh = torch.empty(fam, dtype=torch.float32, pin_memory=True)
+        Xd2 = torch.empty_like(Xd)
+        outd = torch.empty(fam, dtype=torch.float32, device=dev)
+        wsd = torch.empty(binding.workspace_size(w.n, w.m, 0, q32), dtype=torch.uint8, device=dev)
+        for _ in range(max(args.warmup, 1)):
+            Xd2.copy_(Xh, non_blocking=True)
+            binding.score_all_families(Xd2, outd, q=q32, workspace=wsd, check=False)
+            outh.copy_(outd, non_blocking=True)
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            Xd2.copy_(Xh, non_blocking=True)
+            binding.score_all_families(Xd2, outd, q=q32, workspace=wsd, check=False)
+            outh.copy_(outd, non_blocking=True)
+            b.record()
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        e2e_ms = sum(a.elapsed_time(b) for a, b in evs)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * fam * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size()),
+               "d2h_bytes_per_step": int(outh.numel() * outh.element_size()),
+               "ms_per_step": e2e_ms / args.steps}
+        del outh, outd, wsd
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
+        cpu = _cpu_baseline(X, w.n, w.m, args.cpu_seconds)
+
+    peak, peak_kind = _peak_hbm()
+    algo_bytes = 4 * fam  # the fp32 score table written once
+    achieved = algo_bytes / (walk_mean / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "m": w.m, "n": w.n, "families": fam,
+                   "q": q32 or binding.auto_q(w.m, 0), "precision": "fp32 walk, fp64 CholeskyQR2 R0",
+                   "l2": "256 MiB buffer zeroed between timed steps (> 129 MB L2); each step "
+                         "also writes a 3.49 GB table",
+                   "parallelism": f"replicas x{world}, one dataset per GPU"},
+        "fp64": fp64,
+        "speedup_fp32_vs_fp64": (value / world) / fp64["value"] if fp64 else None,
+        "walk_ms": walk_mean,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": _traffic(w.name),
+                     "peak_kind": peak_kind, "kernel": "walk_kernel",
+                     "algorithmic_bytes_per_launch": algo_bytes},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,114 @@
+/*
+ * givensbn.h -- C ABI of the GB300 library that scores every family of a
+ * Gaussian Bayesian network by the Givens-rotation walk of arXiv 1901.07643.
+ *
+ * A family is a child variable c and a parent set S of the other variables;
+ * m variables give m * 2^(m-1) families (Sec. 1).  For each family the
+ * library computes the residual sum of squares RSS(c|S) of the least-squares
+ * regression of the centred column c on the centred columns S, exactly up to
+ * rounding (Sec. 1 and Sec. 2), and stores the BIC-style local score
+ *
+ *     score(c|S) = n * ln(RSS / n) + |S| * ln(n)          (lower is better)
+ *
+ * at table slot idx(c,S) = c * 2^(m-1) + compress(S, c), where compress
+ * deletes bit c from the m-bit parent mask (child-major table, one
+ * (m-1)-bit parent mask per child).  RSS == 0 (exact collinearity) gives -inf.
+ *
+ * How: one FP64 QR R0 of the centred n x m data (CholeskyQR2), then the
+ * greedy sequence of adjacent column transpositions of Algorithm 1, each
+ * re-triangularised by one Givens rotation (the GRC operator of Sec. 1.3);
+ * every R on the walk yields the RSS of the families whose parents are a
+ * prefix of its column ordering (Sec. 2).  The sequence is split into
+ * independent sub-walks as in Sec. 7 (Algorithm 2, corrected reading), one
+ * per GPU lane.
+ *
+ * Conventions for every entry point:
+ *  - Pointers marked "device" are CUDA device pointers on the current device;
+ *    pointers marked "host" are ordinary host memory.  The caller owns all
+ *    buffers; the library allocates nothing.  Scratch memory is the caller's
+ *    workspace, sized by givensbn_workspace_size().
+ *  - Work is enqueued on opts->stream (NULL = legacy default stream) and the
+ *    call returns without synchronising.  Device-side conditions (a
+ *    rank-deficient Gram matrix) are recorded in the workspace and read with
+ *    givensbn_status(), which synchronises the stream.
+ *  - Return value: 0 on success, a negative GBN_ERR_* code otherwise; no work
+ *    has been enqueued when an argument error is returned.
+ *  - X is row-major n x m FP64 (row t, column j at X[t*m + j]), raw (the
+ *    library centres the columns unless opts->center == 0).
+ */
+#ifndef GIVENSBN_H
+#define GIVENSBN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* error codes */
+#define GBN_OK 0
+#define GBN_ERR_M (-1)          /* m outside [GBN_MIN_M, GBN_MAX_M] */
+#define GBN_ERR_N (-2)          /* n < m + 1 */
+#define GBN_ERR_NULL (-3)       /* a required pointer is NULL */
+#define GBN_ERR_ALIGN (-4)      /* a pointer is not 16-byte aligned */
+#define GBN_ERR_WORKSPACE (-5)  /* workspace missing or smaller than required */
+#define GBN_ERR_CUDA (-6)       /* a CUDA launch or runtime call failed */
+#define GBN_ERR_Q (-7)          /* opts->q outside the supported range for m */
+#define GBN_ERR_PRECISION (-8)  /* opts->precision not 0 or 1 */
+#define GBN_ERR_BATCH (-9)      /* batched arguments inconsistent */
+
+/* device status bits (givensbn_status) */
+#define GBN_STATUS_RANK_DEFICIENT 1 /* a Cholesky pivot was <= 0: RSS 0 for some families */
+
+#define GBN_MIN_M 2
+#define GBN_MAX_M 30
+
+typedef struct givensbn_opts {
+    int32_t precision;      /* 0: FP32 rotations and fp32 scores; 1: FP64 throughout, fp64 scores */
+    int32_t center;         /* 1 (default): centre the columns of X first */
+    int32_t q;              /* variables per sub-walk (0 = automatic choice) */
+    int32_t debug_coverage; /* 1: instead of scores, add 1 to a uint32 counter per table slot */
+    void* stream;           /* cudaStream_t, NULL for the default stream */
+    void* workspace;        /* device scratch, >= givensbn_workspace_size() bytes, 256-byte aligned */
+    size_t workspace_bytes;
+    void* stage_events;     /* NULL, or host array of 4 cudaEvent_t recorded on the stream before
+                               the R0 stage, after it, after the sub-walk roots and after the walk */
+} givensbn_opts;
+
+/* Default options: FP32, centring on, automatic q, no workspace. */
+void givensbn_default_opts(givensbn_opts* opts);
+
+/*
+ * Bytes of device workspace score_all_families needs for (n, m) with these
+ * options (precision and q matter).  Writes *bytes; returns 0 or GBN_ERR_*.
+ */
+int givensbn_workspace_size(int64_t n, int32_t m, const givensbn_opts* opts, size_t* bytes);
+
+/*
+ * Scores of every family of the n x m data X (the problem of Sec. 1;
+ * method of Sec. 1.3, Sec. 3 and Sec. 7).
+ *   X          device, n x m FP64 row-major, read only
+ *   out_scores device, m * 2^(m-1) elements: float (precision 0) or double
+ *              (precision 1), or uint32 counters if opts->debug_coverage;
+ *              every element is written exactly once
+ *   opts       host; workspace required
+ */
+int score_all_families(const double* X, int64_t n, int32_t m, void* out_scores,
+                       const givensbn_opts* opts);
+
+/* Device status word recorded by the last call that used this workspace
+ * (GBN_STATUS_* bits).  Synchronises opts->stream.  Returns 0 or GBN_ERR_*. */
+int givensbn_status(const givensbn_opts* opts, int32_t* status);
+
+/* Human-readable text for a GBN_ERR_* code (static storage). */
+const char* givensbn_strerror(int code);
+
+/* The q the automatic choice picks for (m, precision). */
+int32_t givensbn_auto_q(int32_t m, int32_t precision);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GIVENSBN_H */

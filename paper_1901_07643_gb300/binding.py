@@ -1,0 +1,147 @@
+"""ctypes binding of libgivensbn (argument marshalling only).
+
+Every step of the scoring path runs in the CUDA library; these functions only
+turn torch tensors into pointers, size the workspace and translate error
+codes.  There is no CPU fallback: if the library is not built or the tensors
+are not on a CUDA device, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+import warnings
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libgivensbn.so")
+_lock = threading.Lock()
+_lib = None
+
+GBN_STATUS_RANK_DEFICIENT = 1
+
+
+class Opts(ctypes.Structure):
+    """Mirror of givensbn_opts (include/givensbn.h)."""
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("center", ctypes.c_int32),
+        ("q", ctypes.c_int32),
+        ("debug_coverage", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_size_t),
+        ("stage_events", ctypes.c_void_p),
+    ]
+
+
+def load():
+    """Load libgivensbn.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"libgivensbn.so not found at {LIB_PATH}; build it with "
+                    "`python -m paper_1901_07643_gb300.build`")
+            lib = ctypes.CDLL(LIB_PATH)
+            P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+            lib.givensbn_default_opts.argtypes = [ctypes.POINTER(Opts)]
+            lib.givensbn_workspace_size.argtypes = [i64, i32, ctypes.POINTER(Opts),
+                                                    ctypes.POINTER(ctypes.c_size_t)]
+            lib.score_all_families.argtypes = [P, i64, i32, P, ctypes.POINTER(Opts)]
+            lib.givensbn_status.argtypes = [ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_int32)]
+            lib.givensbn_strerror.argtypes = [ctypes.c_int]
+            lib.givensbn_strerror.restype = ctypes.c_char_p
+            lib.givensbn_auto_q.argtypes = [i32, i32]
+            lib.givensbn_auto_q.restype = i32
+            _lib = lib
+    return _lib
+
+
+class GivensBNError(RuntimeError):
+    def __init__(self, code: int):
+        super().__init__(f"givensbn error {code}: {strerror(code)}")
+        self.code = code
+
+
+def strerror(code: int) -> str:
+    return load().givensbn_strerror(code).decode()
+
+
+def auto_q(m: int, precision: int = 0) -> int:
+    return int(load().givensbn_auto_q(m, precision))
+
+
+def _opts(precision=0, q=0, center=True, debug_coverage=False, stream=None,
+          workspace=None, stage_events=None) -> Opts:
+    o = Opts()
+    load().givensbn_default_opts(ctypes.byref(o))
+    o.precision = int(precision)
+    o.q = int(q)
+    o.center = 1 if center else 0
+    o.debug_coverage = 1 if debug_coverage else 0
+    o.stream = stream
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    if stage_events is not None:
+        arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in stage_events])
+        o._events_keepalive = arr
+        o.stage_events = ctypes.cast(arr, ctypes.c_void_p)
+    return o
+
+
+def workspace_size(n: int, m: int, precision: int = 0, q: int = 0) -> int:
+    o = _opts(precision, q)
+    b = ctypes.c_size_t(0)
+    rc = load().givensbn_workspace_size(n, m, ctypes.byref(o), ctypes.byref(b))
+    if rc:
+        raise GivensBNError(rc)
+    return int(b.value)
+
+
+def _stream_handle(stream, device):
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def score_all_families(X: torch.Tensor, out: torch.Tensor | None = None, *, precision: int = 0,
+                       q: int = 0, center: bool = True, debug_coverage: bool = False,
+                       workspace: torch.Tensor | None = None, stream=None,
+                       stage_events=None, check: bool = True) -> torch.Tensor:
+    """Scores of all m * 2^(m-1) families of the n x m data X (CUDA float64, row-major).
+
+    Returns a 1-D tensor in table layout (float32 for precision 0, float64 for
+    precision 1, int32 counters for debug_coverage).  check=True synchronises
+    and warns if the data were rank deficient.  stage_events: four
+    torch.cuda.Event(enable_timing=True) recorded at the stage boundaries.
+    """
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float64 and X.dim() == 2):
+        raise TypeError("X must be a 2-D float64 CUDA tensor")
+    X = X.contiguous()
+    n, m = X.shape
+    dev = X.device
+    if out is None:
+        size = m << (m - 1)
+        if debug_coverage:
+            out = torch.zeros(size, dtype=torch.int32, device=dev)
+        else:
+            out = torch.empty(size, dtype=torch.float64 if precision else torch.float32, device=dev)
+    if workspace is None:
+        workspace = torch.empty(workspace_size(n, m, precision, q), dtype=torch.uint8, device=dev)
+    o = _opts(precision, q, center, debug_coverage, _stream_handle(stream, dev), workspace,
+              stage_events)
+    rc = load().score_all_families(ctypes.c_void_p(X.data_ptr()), n, m,
+                                   ctypes.c_void_p(out.data_ptr()), ctypes.byref(o))
+    if rc:
+        raise GivensBNError(rc)
+    if check:
+        st = ctypes.c_int32(0)
+        rc = load().givensbn_status(ctypes.byref(o), ctypes.byref(st))
+        if rc:
+            raise GivensBNError(rc)
+        if st.value & GBN_STATUS_RANK_DEFICIENT:
+            warnings.warn("givensbn: data rank deficient; some RSS are 0 (scores -inf)")
+    return out

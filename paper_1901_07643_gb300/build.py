@@ -1,0 +1,100 @@
+"""Build libgivensbn.so (sm_103a) in-tree from csrc/ with nvcc, objects compiled in parallel.
+
+Usage: python -m paper_1901_07643_gb300.build [--force] [--jobs N]
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import glob
+import os
+import subprocess
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+OBJ = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "lib", "libgivensbn.so")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo",
+                     "-Xcompiler", "-fPIC", "-I", INCLUDE]
+
+# (scalar type, Q) pairs the dispatcher references
+WALK_INSTANCES = [("float", q) for q in range(2, 9)] + [("double", q) for q in range(2, 8)]
+
+
+def _nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if cand and (os.path.isabs(cand) and os.path.exists(cand) or not os.path.isabs(cand)):
+            return cand
+    return "nvcc"
+
+
+def _jobs():
+    src_common = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "givensbn.h")]
+    jobs = []
+    for name in ("r0", "roots", "api", "walk_dispatch"):
+        src = os.path.join(CSRC, name + ".cu")
+        jobs.append((os.path.join(OBJ, name + ".o"), [src], [src] + src_common, []))
+    inst = os.path.join(CSRC, "walk_inst.cu")
+    for t, q in WALK_INSTANCES:
+        for cov in (0, 1):
+            obj = os.path.join(OBJ, f"walk_{t}_q{q}_c{cov}.o")
+            jobs.append((obj, [inst], [inst] + src_common,
+                         [f"-DGBN_T={t}", f"-DGBN_Q={q}", f"-DGBN_COV={cov}"]))
+    return jobs
+
+
+def _stale(target: str, deps) -> bool:
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, jobs: int = 0, verbose: bool = False) -> str:
+    os.makedirs(OBJ, exist_ok=True)
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    nvcc = _nvcc()
+    todo = [j for j in _jobs() if force or _stale(j[0], j[2])]
+    t0 = time.time()
+
+    def run(job):
+        obj, srcs, _, defs = job
+        tmp = obj + f".tmp{os.getpid()}"
+        cmd = [nvcc] + NVCC_FLAGS + defs + ["-c", srcs[0], "-o", tmp]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {obj}:\n{r.stderr}")
+        os.replace(tmp, obj)
+        return obj
+
+    if todo:
+        workers = jobs or max(1, os.cpu_count() or 1)
+        # largest instantiations first so the pool finishes together
+        todo.sort(key=lambda j: -(("q8" in j[0]) * 4 + ("q7" in j[0]) * 3 + ("q6" in j[0]) * 2))
+        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+            for obj in ex.map(run, todo):
+                if verbose:
+                    print(f"  built {os.path.basename(obj)} ({time.time() - t0:.0f}s)", flush=True)
+    objs = [j[0] for j in _jobs()]
+    if force or todo or _stale(LIB, objs):
+        tmp = LIB + f".tmp{os.getpid()}"
+        cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB)
+    if verbose:
+        print(f"libgivensbn.so ready ({time.time() - t0:.0f}s)")
+    return LIB
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--force", action="store_true")
+    ap.add_argument("--jobs", type=int, default=0)
+    a = ap.parse_args()
+    build(force=a.force, jobs=a.jobs, verbose=True)
+    sys.exit(0)

@@ -1,0 +1,144 @@
+// C ABI of libgivensbn: argument checks, the execution plan and the stage launches.
+#include <math.h>
+#include <string.h>
+
+#include "gbn_internal.cuh"
+
+namespace gbn {
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static int max_q(int precision) { return precision ? 7 : kMaxQ; }
+
+int auto_q(int m, int precision) {
+    // Enough CTAs (2^(m-Q-5)) to fill the GPU several times over once m is
+    // large, and never more free variables than the register-resident block
+    // and the shared-memory tape hold.
+    int q = m - 14;
+    if (q < 4) q = 4;
+    if (q > max_q(precision)) q = max_q(precision);
+    if (q > m) q = m;
+    return q;
+}
+
+int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
+    if (m < GBN_MIN_M || m > GBN_MAX_M) return GBN_ERR_M;
+    if (n < (int64_t)m + 1) return GBN_ERR_N;
+    const int precision = opts ? opts->precision : 0;
+    if (precision != 0 && precision != 1) return GBN_ERR_PRECISION;
+    int Q = (opts && opts->q > 0) ? opts->q : auto_q(m, precision);
+    if (Q < kMinQ || Q > max_q(precision) || Q > m) return GBN_ERR_Q;
+    *p = Plan();
+    p->m = m;
+    p->n = n;
+    p->precision = precision;
+    p->Q = Q;
+    p->k = m - Q;
+    p->W = p->k < kLaneBits ? p->k : kLaneBits;
+    p->lanes = 1 << p->W;
+    p->n_cta = (int64_t)1 << (p->k - p->W);
+    int pos = 0;
+    for (int v = p->W; v < p->k; ++v) p->order[pos++] = v;
+    for (int v = 0; v < p->W; ++v) p->order[pos++] = v;
+    for (int v = p->k; v < m; ++v) p->order[pos++] = v;
+    int panels = (int)(n / 16);
+    if (panels < 1) panels = 1;
+    if (panels > kMaxPanels) panels = kMaxPanels;
+    p->rows_per_panel = (int)((n + panels - 1) / panels);
+    p->panels = (int)((n + p->rows_per_panel - 1) / p->rows_per_panel);
+    p->center = opts ? (opts->center != 0) : 1;
+    p->coverage = opts ? (opts->debug_coverage != 0) : 0;
+    const size_t es = precision ? sizeof(double) : sizeof(float);
+    p->leaf_stride = leaf_stride_elems(Q, p->k);
+    size_t off = 0;
+    p->off_status = off;
+    off = align_up(off + 256, 256);
+    p->off_colsum = off;
+    off = align_up(off + sizeof(double) * (size_t)p->panels * m, 256);
+    p->off_gram = off;
+    off = align_up(off + sizeof(double) * (size_t)p->panels * (m * (m + 1) / 2), 256);
+    p->off_r1 = off;
+    off = align_up(off + sizeof(double) * (size_t)m * m, 256);
+    p->off_r0 = off;
+    off = align_up(off + sizeof(double) * (size_t)m * m, 256);
+    p->off_leaves = off;
+    off = align_up(off + es * p->leaf_stride * (size_t)p->n_cta, 256);
+    p->total_bytes = off;
+    return GBN_OK;
+}
+
+}  // namespace gbn
+
+using namespace gbn;
+
+extern "C" {
+
+void givensbn_default_opts(givensbn_opts* opts) {
+    if (!opts) return;
+    memset(opts, 0, sizeof(*opts));
+    opts->center = 1;
+}
+
+int32_t givensbn_auto_q(int32_t m, int32_t precision) { return auto_q(m, precision); }
+
+int givensbn_workspace_size(int64_t n, int32_t m, const givensbn_opts* opts, size_t* bytes) {
+    if (!bytes) return GBN_ERR_NULL;
+    Plan p;
+    const int rc = make_plan(n, m, opts, &p);
+    if (rc) return rc;
+    *bytes = p.total_bytes;
+    return GBN_OK;
+}
+
+int score_all_families(const double* X, int64_t n, int32_t m, void* out_scores,
+                       const givensbn_opts* opts) {
+    if (!opts) return GBN_ERR_NULL;
+    Plan p;
+    int rc = make_plan(n, m, opts, &p);
+    if (rc) return rc;
+    if (!X || !out_scores) return GBN_ERR_NULL;
+    if (((uintptr_t)X & 7u) || ((uintptr_t)out_scores & 15u)) return GBN_ERR_ALIGN;
+    if (!opts->workspace || opts->workspace_bytes < p.total_bytes) return GBN_ERR_WORKSPACE;
+    if ((uintptr_t)opts->workspace & 255u) return GBN_ERR_ALIGN;
+    char* ws = static_cast<char*>(opts->workspace);
+    cudaStream_t stream = static_cast<cudaStream_t>(opts->stream);
+    cudaEvent_t* ev = static_cast<cudaEvent_t*>(opts->stage_events);
+    if (ev && cudaEventRecord(ev[0], stream) != cudaSuccess) return GBN_ERR_CUDA;
+    if ((rc = launch_r0(p, X, ws, stream))) return rc;
+    if (ev && cudaEventRecord(ev[1], stream) != cudaSuccess) return GBN_ERR_CUDA;
+    if ((rc = launch_roots(p, ws, stream))) return rc;
+    if (ev && cudaEventRecord(ev[2], stream) != cudaSuccess) return GBN_ERR_CUDA;
+    if ((rc = launch_walk(p, ws, out_scores, stream))) return rc;
+    if (ev && cudaEventRecord(ev[3], stream) != cudaSuccess) return GBN_ERR_CUDA;
+    return GBN_OK;
+}
+
+int givensbn_status(const givensbn_opts* opts, int32_t* status) {
+    if (!opts || !status || !opts->workspace) return GBN_ERR_NULL;
+    cudaStream_t stream = static_cast<cudaStream_t>(opts->stream);
+    int32_t v = 0;
+    if (cudaMemcpyAsync(&v, opts->workspace, sizeof(v), cudaMemcpyDeviceToHost, stream) !=
+        cudaSuccess)
+        return GBN_ERR_CUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return GBN_ERR_CUDA;
+    *status = v;
+    return GBN_OK;
+}
+
+const char* givensbn_strerror(int code) {
+    switch (code) {
+        case GBN_OK: return "success";
+        case GBN_ERR_M: return "m outside the supported range [2, 30]";
+        case GBN_ERR_N: return "n must be at least m + 1";
+        case GBN_ERR_NULL: return "a required pointer is NULL";
+        case GBN_ERR_ALIGN: return "a pointer is misaligned";
+        case GBN_ERR_WORKSPACE: return "workspace missing or too small";
+        case GBN_ERR_CUDA: return "CUDA launch or runtime error";
+        case GBN_ERR_Q: return "q outside the supported range";
+        case GBN_ERR_PRECISION: return "precision must be 0 (FP32) or 1 (FP64)";
+        case GBN_ERR_BATCH: return "inconsistent batched arguments";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// Internal declarations shared by the CUDA translation units of libgivensbn.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/givensbn.h"
+
+namespace gbn {
+
+constexpr int kMaxQ = 8;     // largest sub-walk size compiled
+constexpr int kMinQ = 2;
+constexpr int kLaneBits = 5; // sub-walks per warp = 2^kLaneBits (one per lane)
+
+// Row-panel count for the tall-skinny passes over X.
+constexpr int kMaxPanels = 304;
+
+// Execution plan of one scoring call (host side, passed to kernels by value).
+struct Plan {
+    int m = 0;        // variables
+    int64_t n = 0;    // samples
+    int precision = 0;
+    int Q = 0;        // variables per sub-walk (the free block, walked by Algorithm 1)
+    int k = 0;        // fixed variables = m - Q (the bits of Algorithm 2's processor code)
+    int W = 0;        // fixed variables that vary across the lanes of a warp, min(5, k)
+    int lanes = 0;    // 2^W sub-walks per CTA
+    int64_t n_cta = 0;  // 2^(k-W) CTAs
+    int order[32] = {}; // column order of R0: [W..k-1, 0..W-1, k..m-1]
+    int panels = 0;
+    int rows_per_panel = 0;
+    int center = 1;
+    int coverage = 0;
+    // workspace layout (byte offsets)
+    size_t off_status = 0, off_colsum = 0, off_gram = 0, off_r1 = 0, off_r0 = 0, off_leaves = 0;
+    size_t total_bytes = 0;
+    size_t leaf_stride = 0;  // elements per CTA leaf record
+};
+
+int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* plan);
+
+// Stages (each enqueues kernels on `stream`; return GBN_OK or GBN_ERR_CUDA).
+int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream);
+int launch_roots(const Plan& p, char* ws, cudaStream_t stream);
+int launch_walk(const Plan& p, char* ws, void* out, cudaStream_t stream);
+
+// Leaf record of one CTA (2^W sub-walk roots), elements of the scalar type,
+// lane-interleaved so that lane l of a warp reads element e at [e*32 + l]:
+//   [0, LQ*32)                 L block, packed upper triangle, e = p(p+1)/2 + r
+//   [LQ*32, LQ*32 + k(Q+1)*32) per fixed variable v: rows 0..Q-1 of its column
+//                              in the sub-walk basis, then its residual C
+inline size_t leaf_stride_elems(int Q, int k) {
+    return (size_t)32 * ((size_t)Q * (Q + 1) / 2 + (size_t)k * (Q + 1));
+}
+
+// ---------------------------------------------------------------------------
+// The greedy transposition sequence of Algorithm 1 (GreedySwaps), generated at
+// compile time for a sub-walk of Q variables, plus what every step reads out.
+// Positions and swap indices are 1-based as in the paper; the stored tables
+// use 0-based positions.
+template <int Q>
+struct WalkSeq {
+    static constexpr int N = (1 << Q) - Q - 1;  // |Upsilon(Q)|, Sec. 3
+    int idx[N > 0 ? N : 1];                     // swap index i (1-based) of step t
+    unsigned prefix[N > 0 ? N : 1];             // local variables at positions 1..i after step t
+    int var_at[N > 0 ? N : 1][Q];               // local variable at each position after step t
+};
+
+template <int Q>
+constexpr WalkSeq<Q> make_walk_seq() {
+    WalkSeq<Q> s{};
+    int buf[(1 << Q) + 1] = {};
+    int len = 0;
+    if (Q >= 2) {
+        buf[0] = 1;  // Upsilon(2) = [1]
+        len = 1;
+    }
+    // Upsilon(j+1) = Upsilon(j) : [j .. 1] : (Upsilon(j) + 1)   (Sec. 3, Sec. 5)
+    for (int j = 2; j < Q; ++j) {
+        const int old = len;
+        for (int i = j; i >= 1; --i) buf[len++] = i;
+        for (int t = 0; t < old; ++t) buf[len++] = buf[t] + 1;
+    }
+    int pos[Q > 0 ? Q : 1] = {};
+    for (int p = 0; p < Q; ++p) pos[p] = p;
+    for (int t = 0; t < len; ++t) {
+        const int i = buf[t];
+        const int tmp = pos[i - 1];
+        pos[i - 1] = pos[i];
+        pos[i] = tmp;
+        s.idx[t] = i;
+        unsigned mask = 0;
+        for (int p = 0; p < i; ++p) mask |= 1u << pos[p];
+        s.prefix[t] = mask;
+        for (int p = 0; p < Q; ++p) s.var_at[t][p] = pos[p];
+    }
+    return s;
+}
+
+template <int Q>
+inline constexpr WalkSeq<Q> kWalkSeq = make_walk_seq<Q>();
+
+}  // namespace gbn

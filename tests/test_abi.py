@@ -1,0 +1,94 @@
+"""The C ABI library loads, exports what include/givensbn.h declares, and checks
+its arguments on the host (no GPU needed for any of this)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import oracle.sequence as seq
+from paper_1901_07643_gb300 import binding
+from paper_1901_07643_gb300 import build as gbn_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "givensbn.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(binding.LIB_PATH):
+        gbn_build.build()
+    return binding.load()
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(\w+)\s*\(", text, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert "score_all_families" in names and len(names) >= 6
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if ln.strip()}
+    for n in names:
+        assert n in exported, n
+        assert hasattr(lib, n)
+
+
+def _ws(n, m, **kw):
+    return binding.workspace_size(n, m, **kw)
+
+
+def test_workspace_size_and_plan(lib):
+    assert _ws(200, 10) > 0
+    assert _ws(5000, 26) > _ws(1000, 20)
+    assert _ws(1000, 20, precision=1) > _ws(1000, 20, precision=0)
+    for m in range(2, 31):
+        q = binding.auto_q(m, 0)
+        assert 2 <= q <= min(8, m)
+        assert binding.auto_q(m, 1) <= 7
+
+
+@pytest.mark.parametrize("n,m,kw,code", [
+    (200, 1, {}, -1), (200, 31, {}, -1), (10, 10, {}, -2), (3, 3, {}, -2),
+    (200, 10, {"precision": 2}, -8), (200, 10, {"q": 9}, -7), (200, 10, {"q": 1}, -7),
+    (200, 4, {"q": 5}, -7), (200, 20, {"q": 8, "precision": 1}, -7),
+])
+def test_argument_errors(lib, n, m, kw, code):
+    with pytest.raises(binding.GivensBNError) as e:
+        _ws(n, m, **kw)
+    assert e.value.code == code
+
+
+def test_entry_point_rejects_before_any_device_work(lib):
+    o = binding._opts()
+    fake = ctypes.c_void_p(1 << 20)
+    assert lib.score_all_families(fake, 200, 1, fake, ctypes.byref(o)) == -1
+    assert lib.score_all_families(None, 200, 10, fake, ctypes.byref(o)) == -3
+    assert lib.score_all_families(fake, 200, 10, fake, None) == -3
+    assert lib.score_all_families(fake, 200, 10, fake, ctypes.byref(o)) == -5  # no workspace
+    assert lib.score_all_families(ctypes.c_void_p((1 << 20) + 4), 200, 10, fake,
+                                  ctypes.byref(o)) == -4
+    assert "workspace" in binding.strerror(-5)
+
+
+def test_device_swap_tables_match_greedy_swaps(tmp_path):
+    """The walk's compile-time tables equal Algorithm 1 and the orderings it visits."""
+    exe = tmp_path / "seq_dump"
+    src = os.path.join(ROOT, "tests", "native", "seq_dump.cu")
+    subprocess.run([gbn_build._nvcc(), "-std=c++17", "--expt-relaxed-constexpr", "-o", str(exe),
+                    src], check=True, capture_output=True)
+    rows = [list(map(int, ln.split())) for ln in
+            subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()]
+    for Q in range(2, 9):
+        mine = [r for r in rows if r[0] == Q]
+        sw = seq.greedy_swaps(Q)
+        assert [r[1] for r in mine] == sw
+        orders = seq.apply_swaps(list(range(Q)), sw)[1:]
+        for r, o, i in zip(mine, orders, sw):
+            assert r[3:] == o
+            assert r[2] == sum(1 << v for v in o[:i])
