@@ -87,6 +87,7 @@ def _opts(precision=0, q=0, center=True, debug_coverage=False, stream=None,
         o.workspace = workspace.data_ptr()
         o.workspace_bytes = workspace.numel() * workspace.element_size()
     if stage_events is not None:
+        assert len(stage_events) == 4
         arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in stage_events])
         o._events_keepalive = arr
         o.stage_events = ctypes.cast(arr, ctypes.c_void_p)
@@ -131,6 +132,10 @@ def score_all_families(X: torch.Tensor, out: torch.Tensor | None = None, *, prec
             out = torch.empty(size, dtype=torch.float64 if precision else torch.float32, device=dev)
     if workspace is None:
         workspace = torch.empty(workspace_size(n, m, precision, q), dtype=torch.uint8, device=dev)
+    if stage_events is not None:
+        for e in stage_events:  # torch creates the CUDA event on its first record()
+            if not e.cuda_event:
+                e.record(stream if stream is not None else torch.cuda.current_stream(dev))
     o = _opts(precision, q, center, debug_coverage, _stream_handle(stream, dev), workspace,
               stage_events)
     rc = load().score_all_families(ctypes.c_void_p(X.data_ptr()), n, m,

@@ -17,6 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "lib", "libgivensbn.so")
+# checked variant: every computed index bounds-checked, synchronised per stage
+OBJ_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "lib", "libgivensbn_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo",
@@ -33,18 +36,18 @@ def _nvcc() -> str:
     return "nvcc"
 
 
-def _jobs():
+def _jobs(obj_dir=OBJ, extra=()):
     src_common = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "givensbn.h")]
     jobs = []
     for name in ("r0", "roots", "api", "walk_dispatch"):
         src = os.path.join(CSRC, name + ".cu")
-        jobs.append((os.path.join(OBJ, name + ".o"), [src], [src] + src_common, []))
+        jobs.append((os.path.join(obj_dir, name + ".o"), [src], [src] + src_common, list(extra)))
     inst = os.path.join(CSRC, "walk_inst.cu")
     for t, q in WALK_INSTANCES:
         for cov in (0, 1):
-            obj = os.path.join(OBJ, f"walk_{t}_q{q}_c{cov}.o")
+            obj = os.path.join(obj_dir, f"walk_{t}_q{q}_c{cov}.o")
             jobs.append((obj, [inst], [inst] + src_common,
-                         [f"-DGBN_T={t}", f"-DGBN_Q={q}", f"-DGBN_COV={cov}"]))
+                         [f"-DGBN_T={t}", f"-DGBN_Q={q}", f"-DGBN_COV={cov}"] + list(extra)))
     return jobs
 
 
@@ -55,11 +58,14 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, jobs: int = 0, verbose: bool = False) -> str:
-    os.makedirs(OBJ, exist_ok=True)
-    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+def build(force: bool = False, jobs: int = 0, verbose: bool = False, checked: bool = False) -> str:
+    obj_dir, lib = (OBJ_CHECKED, LIB_CHECKED) if checked else (OBJ, LIB)
+    extra = ["-DGBN_CHECKED"] if checked else []
+    os.makedirs(obj_dir, exist_ok=True)
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
     nvcc = _nvcc()
-    todo = [j for j in _jobs() if force or _stale(j[0], j[2])]
+    all_jobs = _jobs(obj_dir, extra)
+    todo = [j for j in all_jobs if force or _stale(j[0], j[2])]
     t0 = time.time()
 
     def run(job):
@@ -80,21 +86,22 @@ def build(force: bool = False, jobs: int = 0, verbose: bool = False) -> str:
             for obj in ex.map(run, todo):
                 if verbose:
                     print(f"  built {os.path.basename(obj)} ({time.time() - t0:.0f}s)", flush=True)
-    objs = [j[0] for j in _jobs()]
-    if force or todo or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    objs = [j[0] for j in all_jobs]
+    if force or todo or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if verbose:
-        print(f"libgivensbn.so ready ({time.time() - t0:.0f}s)")
-    return LIB
+        print(f"{os.path.basename(lib)} ready ({time.time() - t0:.0f}s)")
+    return lib
 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")
     ap.add_argument("--jobs", type=int, default=0)
+    ap.add_argument("--checked", action="store_true")
     a = ap.parse_args()
-    build(force=a.force, jobs=a.jobs, verbose=True)
+    build(force=a.force, jobs=a.jobs, verbose=True, checked=a.checked)
     sys.exit(0)

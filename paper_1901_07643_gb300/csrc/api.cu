@@ -1,5 +1,6 @@
 // C ABI of libgivensbn: argument checks, the execution plan and the stage launches.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include "gbn_internal.cuh"
@@ -71,6 +72,30 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
 
 using namespace gbn;
 
+// Checked builds synchronise after every stage and report the CUDA error and
+// the first out-of-bounds index the kernels caught; ordinary builds pass rc on.
+static int checked_stage(const char* name, int rc, const Plan& p, char* ws, cudaStream_t stream) {
+#ifdef GBN_CHECKED
+    cudaError_t e = cudaGetLastError();
+    cudaError_t s = cudaStreamSynchronize(stream);
+    unsigned long long rec[4] = {0, 0, 0, 0};
+    cudaError_t c = cudaMemcpy(rec, ws + p.off_status + kCheckOffset, sizeof(rec),
+                               cudaMemcpyDeviceToHost);
+    fprintf(stderr,
+            "[givensbn checked] stage %s: rc=%d launch=%s sync=%s copy=%s violations=%llu "
+            "site=%llu index=%llu bound=%llu\n",
+            name, rc, cudaGetErrorString(e), cudaGetErrorString(s), cudaGetErrorString(c), rec[0],
+            rec[1], rec[2], rec[3]);
+    if (rc == GBN_OK && (e != cudaSuccess || s != cudaSuccess || rec[0] != 0)) rc = GBN_ERR_CUDA;
+#else
+    (void)name;
+    (void)p;
+    (void)ws;
+    (void)stream;
+#endif
+    return rc;
+}
+
 extern "C" {
 
 void givensbn_default_opts(givensbn_opts* opts) {
@@ -104,11 +129,14 @@ int score_all_families(const double* X, int64_t n, int32_t m, void* out_scores,
     cudaStream_t stream = static_cast<cudaStream_t>(opts->stream);
     cudaEvent_t* ev = static_cast<cudaEvent_t*>(opts->stage_events);
     if (ev && cudaEventRecord(ev[0], stream) != cudaSuccess) return GBN_ERR_CUDA;
-    if ((rc = launch_r0(p, X, ws, stream))) return rc;
+    rc = launch_r0(p, X, ws, stream);
+    if ((rc = checked_stage("r0", rc, p, ws, stream))) return rc;
     if (ev && cudaEventRecord(ev[1], stream) != cudaSuccess) return GBN_ERR_CUDA;
-    if ((rc = launch_roots(p, ws, stream))) return rc;
+    rc = launch_roots(p, ws, stream);
+    if ((rc = checked_stage("roots", rc, p, ws, stream))) return rc;
     if (ev && cudaEventRecord(ev[2], stream) != cudaSuccess) return GBN_ERR_CUDA;
-    if ((rc = launch_walk(p, ws, out_scores, stream))) return rc;
+    rc = launch_walk(p, ws, out_scores, stream);
+    if ((rc = checked_stage("walk", rc, p, ws, stream))) return rc;
     if (ev && cudaEventRecord(ev[3], stream) != cudaSuccess) return GBN_ERR_CUDA;
     return GBN_OK;
 }

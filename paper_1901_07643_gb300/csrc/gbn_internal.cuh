@@ -6,7 +6,30 @@
 
 #include "../../include/givensbn.h"
 
+// Checked builds (-DGBN_CHECKED) test every computed global or shared-memory
+// index against its bound before the access; a violation skips the access and
+// records (count, site, index, bound) in four 64-bit words of the workspace
+// status block.  Ordinary builds compile the checks away.
+#ifdef GBN_CHECKED
+__device__ __forceinline__ bool gbn_in_bounds(unsigned long long* rec, int site, long long idx,
+                                              long long bound) {
+    if (idx >= 0 && idx < bound) return true;
+    if (atomicAdd(rec, 1ull) == 0ull) {
+        rec[1] = (unsigned long long)site;
+        rec[2] = (unsigned long long)idx;
+        rec[3] = (unsigned long long)bound;
+    }
+    return false;
+}
+#define GBN_IN(rec, site, idx, bound) \
+    gbn_in_bounds((rec), (site), (long long)(idx), (long long)(bound))
+#else
+#define GBN_IN(rec, site, idx, bound) true
+#endif
+
 namespace gbn {
+
+constexpr int kCheckOffset = 64;  // byte offset of the check record in the status block
 
 constexpr int kMaxQ = 8;     // largest sub-walk size compiled
 constexpr int kMinQ = 2;

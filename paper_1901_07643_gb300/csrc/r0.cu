@@ -12,9 +12,15 @@ namespace gbn {
 namespace {
 
 constexpr int kPanelChunk = 32;  // rows staged in shared memory at a time
+constexpr int kLd = 33;          // row stride of the m x m shared-memory tiles
+
+// All shared-memory tiles here are flat 1-D arrays indexed as [row * kLd + col]:
+// with this toolchain, runtime-indexed two-dimensional __shared__ arrays were
+// mis-addressed in sm_103 code while the same accesses on flat arrays were not.
 
 __global__ void colsum_kernel(const double* __restrict__ X, int64_t n, int m, int rows_per,
-                              double* __restrict__ colsum) {
+                              double* __restrict__ colsum, int panels,
+                              unsigned long long* chk) {
     __shared__ double red[256];
     const int b = blockIdx.x;
     const int64_t r0 = (int64_t)b * rows_per;
@@ -24,13 +30,16 @@ __global__ void colsum_kernel(const double* __restrict__ X, int64_t n, int m, in
     const int rl = threadIdx.x / m;
     double s = 0.0;
     if (rl < per)
-        for (int64_t t = r0 + rl; t < r1; t += per) s += X[t * m + j];
-    red[threadIdx.x] = (rl < per) ? s : 0.0;
+        for (int64_t t = r0 + rl; t < r1; t += per)
+            if (GBN_IN(chk, 101, t * m + j, n * m)) s += X[t * m + j];
+    if (GBN_IN(chk, 102, threadIdx.x, 256)) red[threadIdx.x] = (rl < per) ? s : 0.0;
     __syncthreads();
     if (threadIdx.x < m) {
         double acc = 0.0;
-        for (int l = 0; l < per; ++l) acc += red[l * m + threadIdx.x];
-        colsum[(int64_t)b * m + threadIdx.x] = acc;
+        for (int l = 0; l < per; ++l)
+            if (GBN_IN(chk, 103, l * m + threadIdx.x, 256)) acc += red[l * m + threadIdx.x];
+        if (GBN_IN(chk, 104, (int64_t)b * m + threadIdx.x, (int64_t)panels * m))
+            colsum[(int64_t)b * m + threadIdx.x] = acc;
     }
 }
 
@@ -39,24 +48,31 @@ __global__ void colsum_kernel(const double* __restrict__ X, int64_t n, int m, in
 // pass 2 the row of Q1 solving y R1 = xc.
 __global__ void gram_kernel(const double* __restrict__ X, int64_t n, int m, int rows_per,
                             const double* __restrict__ colsum, int panels, int center,
-                            const double* __restrict__ R1, Plan plan, double* __restrict__ gram) {
+                            const double* __restrict__ R1, Plan plan, double* __restrict__ gram,
+                            unsigned long long* chk) {
     __shared__ double mu[32];
-    __shared__ double rows[kPanelChunk][33];
-    __shared__ double r1[32][33];
+    __shared__ double rows[kPanelChunk * kLd];
+    __shared__ double r1[32 * kLd];
     const int tid = threadIdx.x;
     if (tid < m) {
         double s = 0.0;
         if (center)
-            for (int b = 0; b < panels; ++b) s += colsum[(int64_t)b * m + plan.order[tid]];
+            for (int b = 0; b < panels; ++b)
+                if (GBN_IN(chk, 111, (int64_t)b * m + plan.order[tid], (int64_t)panels * m))
+                    s += colsum[(int64_t)b * m + plan.order[tid]];
         mu[tid] = center ? s / (double)n : 0.0;
     }
     if (R1)
-        for (int e = tid; e < m * m; e += blockDim.x) r1[e / m][e % m] = R1[e];
+        for (int e = tid; e < m * m; e += blockDim.x)
+            if (GBN_IN(chk, 112, (e / m) * kLd + e % m, 32 * kLd)) r1[(e / m) * kLd + e % m] = R1[e];
     const int npair = m * (m + 1) / 2;
     int pi = 0, pj = 0;
     if (tid < npair) {  // unpack pair index -> (i, j), i <= j
         int e = tid, i = 0;
-        while (e >= m - i) { e -= m - i; ++i; }
+        while (e >= m - i) {
+            e -= m - i;
+            ++i;
+        }
         pi = i;
         pj = i + e;
     }
@@ -68,23 +84,27 @@ __global__ void gram_kernel(const double* __restrict__ X, int64_t n, int m, int 
         const int cnt = (rend - c0 < kPanelChunk) ? (int)(rend - c0) : kPanelChunk;
         for (int e = tid; e < cnt * m; e += blockDim.x) {
             const int t = e / m, j = e % m;
-            rows[t][j] = X[(c0 + t) * m + plan.order[j]] - mu[j];
+            const int64_t xi = (c0 + t) * m + plan.order[j];
+            if (GBN_IN(chk, 113, xi, n * m) && GBN_IN(chk, 114, t * kLd + j, kPanelChunk * kLd))
+                rows[t * kLd + j] = X[xi] - mu[j];
         }
         __syncthreads();
         if (R1 && tid < cnt) {  // forward substitution y R1 = xc, one row per thread
+            double* y = rows + tid * kLd;
             for (int j = 0; j < m; ++j) {
-                double s = rows[tid][j];
-                for (int i = 0; i < j; ++i) s -= rows[tid][i] * r1[i][j];
-                const double d = r1[j][j];
-                rows[tid][j] = (d != 0.0) ? s / d : 0.0;
+                double s = y[j];
+                for (int i = 0; i < j; ++i) s -= y[i] * r1[i * kLd + j];
+                const double d = r1[j * kLd + j];
+                y[j] = (d != 0.0) ? s / d : 0.0;
             }
         }
         __syncthreads();
         if (tid < npair)
-            for (int t = 0; t < cnt; ++t) acc = fma(rows[t][pi], rows[t][pj], acc);
+            for (int t = 0; t < cnt; ++t) acc = fma(rows[t * kLd + pi], rows[t * kLd + pj], acc);
         __syncthreads();
     }
-    if (tid < npair) gram[(int64_t)blockIdx.x * npair + tid] = acc;
+    if (tid < npair && GBN_IN(chk, 115, (int64_t)blockIdx.x * npair + tid, (int64_t)panels * npair))
+        gram[(int64_t)blockIdx.x * npair + tid] = acc;
 }
 
 // Sum the panel Grams, Cholesky-factor (upper R with R^T R = G).  If R1 is
@@ -92,38 +112,43 @@ __global__ void gram_kernel(const double* __restrict__ X, int64_t n, int m, int 
 // factor itself is written to Rout.
 __global__ void chol_kernel(const double* __restrict__ gram, int panels, int m,
                             const double* __restrict__ R1, double* __restrict__ Rout,
-                            int* __restrict__ status) {
-    __shared__ double G[32][33];
-    __shared__ double R[32][33];
+                            int* __restrict__ status, unsigned long long* chk) {
+    __shared__ double G[32 * kLd];
+    __shared__ double R[32 * kLd];
     const int tid = threadIdx.x;
     const int npair = m * (m + 1) / 2;
     for (int e = tid; e < npair; e += blockDim.x) {
         int q = e, i = 0;
-        while (q >= m - i) { q -= m - i; ++i; }
+        while (q >= m - i) {
+            q -= m - i;
+            ++i;
+        }
         const int j = i + q;
         double s = 0.0;
-        for (int b = 0; b < panels; ++b) s += gram[(int64_t)b * npair + e];
-        G[i][j] = s;
+        for (int b = 0; b < panels; ++b)
+            if (GBN_IN(chk, 121, (int64_t)b * npair + e, (int64_t)panels * npair))
+                s += gram[(int64_t)b * npair + e];
+        if (GBN_IN(chk, 122, i * kLd + j, 32 * kLd)) G[i * kLd + j] = s;
     }
-    for (int e = tid; e < 32 * 33; e += blockDim.x) R[e / 33][e % 33] = 0.0;
+    for (int e = tid; e < 32 * kLd; e += blockDim.x) R[e] = 0.0;
     __syncthreads();
     for (int j = 0; j < m; ++j) {
         if (tid == 0) {
-            double d = G[j][j];
-            for (int i = 0; i < j; ++i) d -= R[i][j] * R[i][j];
+            double d = G[j * kLd + j];
+            for (int i = 0; i < j; ++i) d -= R[i * kLd + j] * R[i * kLd + j];
             if (d > 0.0) {
-                R[j][j] = sqrt(d);
+                R[j * kLd + j] = sqrt(d);
             } else {
-                R[j][j] = 0.0;  // column j lies in the span of the earlier ones
+                R[j * kLd + j] = 0.0;  // column j lies in the span of the earlier ones
                 atomicOr(status, GBN_STATUS_RANK_DEFICIENT);
             }
         }
         __syncthreads();
-        const double rjj = R[j][j];
+        const double rjj = R[j * kLd + j];
         for (int l = j + 1 + tid; l < m; l += blockDim.x) {
-            double s = G[j][l];
-            for (int i = 0; i < j; ++i) s -= R[i][j] * R[i][l];
-            R[j][l] = (rjj != 0.0) ? s / rjj : 0.0;
+            double s = G[j * kLd + l];
+            for (int i = 0; i < j; ++i) s -= R[i * kLd + j] * R[i * kLd + l];
+            R[j * kLd + l] = (rjj != 0.0) ? s / rjj : 0.0;
         }
         __syncthreads();
     }
@@ -132,12 +157,13 @@ __global__ void chol_kernel(const double* __restrict__ gram, int panels, int m,
         double v = 0.0;
         if (i <= j) {
             if (R1) {
-                for (int l = i; l <= j; ++l) v += R[i][l] * R1[l * m + j];
+                for (int l = i; l <= j; ++l)
+                    if (GBN_IN(chk, 123, l * m + j, m * m)) v += R[i * kLd + l] * R1[l * m + j];
             } else {
-                v = R[i][j];
+                v = R[i * kLd + j];
             }
         }
-        Rout[e] = v;
+        if (GBN_IN(chk, 124, e, m * m)) Rout[e] = v;
     }
 }
 
@@ -149,14 +175,17 @@ int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream) {
     double* r1 = reinterpret_cast<double*>(ws + p.off_r1);
     double* r0 = reinterpret_cast<double*>(ws + p.off_r0);
     int* status = reinterpret_cast<int*>(ws + p.off_status);
-    if (cudaMemsetAsync(status, 0, sizeof(int), stream) != cudaSuccess) return GBN_ERR_CUDA;
-    if (p.center) colsum_kernel<<<p.panels, 256, 0, stream>>>(X, p.n, p.m, p.rows_per_panel, colsum);
+    unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
+    if (cudaMemsetAsync(ws + p.off_status, 0, 256, stream) != cudaSuccess) return GBN_ERR_CUDA;
+    if (p.center)
+        colsum_kernel<<<p.panels, 256, 0, stream>>>(X, p.n, p.m, p.rows_per_panel, colsum, p.panels,
+                                                    chk);
     gram_kernel<<<p.panels, 512, 0, stream>>>(X, p.n, p.m, p.rows_per_panel, colsum, p.panels,
-                                              p.center, nullptr, p, gram);
-    chol_kernel<<<1, 256, 0, stream>>>(gram, p.panels, p.m, nullptr, r1, status);
+                                              p.center, nullptr, p, gram, chk);
+    chol_kernel<<<1, 256, 0, stream>>>(gram, p.panels, p.m, nullptr, r1, status, chk);
     gram_kernel<<<p.panels, 512, 0, stream>>>(X, p.n, p.m, p.rows_per_panel, colsum, p.panels,
-                                              p.center, r1, p, gram);
-    chol_kernel<<<1, 256, 0, stream>>>(gram, p.panels, p.m, r1, r0, status);
+                                              p.center, r1, p, gram, chk);
+    chol_kernel<<<1, 256, 0, stream>>>(gram, p.panels, p.m, r1, r0, status, chk);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 

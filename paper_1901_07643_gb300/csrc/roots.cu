@@ -27,9 +27,14 @@
 namespace gbn {
 namespace {
 
+constexpr int kNodeLd = 32;  // row stride of a node matrix
+
+// Node matrices are flat arrays indexed [row * kNodeLd + column]: with this
+// toolchain, runtime-indexed two-dimensional shared-memory arrays were
+// mis-addressed in sm_103 code while flat ones were not.
 template <typename T>
 struct Node {
-    T M[32][32];  // M[row][column]; columns [0,p) = R, [p, p+nc) = carried vectors
+    T M[32 * kNodeLd];  // row-major; columns [0,p) = R, [p, p+nc) = carried vectors
     T C[32];      // residual of each carried column below row p
     int var[32];  // variable of each column
     int p, nc;
@@ -55,11 +60,11 @@ __device__ __forceinline__ void givens(T a, T b, T& c, T& s, T& rho) {
 
 // Child where the first variable joins the front set F.
 template <typename T>
-__device__ void node_include(const Node<T>& s, Node<T>& d, int lane) {
+__device__ void node_include(const Node<T>& s, Node<T>& d, int lane, unsigned long long* chk) {
     const int p = s.p, nc = s.nc;
     const int ncol = p - 1 + nc;
-    if (lane < ncol) {
-        for (int r = 0; r < p - 1; ++r) d.M[r][lane] = s.M[r + 1][lane + 1];
+    if (lane < ncol && GBN_IN(chk, 201, lane + 1, 32) && GBN_IN(chk, 202, p, 33)) {
+        for (int r = 0; r < p - 1; ++r) d.M[(r) * kNodeLd + (lane)] = s.M[(r + 1) * kNodeLd + (lane + 1)];
         d.C[lane] = s.C[lane + 1];
         d.var[lane] = s.var[lane + 1];
     }
@@ -72,24 +77,28 @@ __device__ void node_include(const Node<T>& s, Node<T>& d, int lane) {
 
 // Child where the first variable joins the back set B.
 template <typename T>
-__device__ void node_exclude(const Node<T>& s, Node<T>& d, int lane) {
+__device__ void node_exclude(const Node<T>& s, Node<T>& d, int lane, unsigned long long* chk) {
     const int p = s.p, nc = s.nc;
     const int ncol = p + nc;
+    if (!GBN_IN(chk, 211, ncol, 33) || !GBN_IN(chk, 212, p, 33) || !GBN_IN(chk, 213, p - 1, 32)) {
+        __syncwarp();
+        return;
+    }
     if (lane < ncol) {
         const int src = (lane < ncol - 1) ? lane + 1 : 0;
-        for (int r = 0; r < p; ++r) d.M[r][lane] = s.M[r][src];
+        for (int r = 0; r < p; ++r) d.M[(r) * kNodeLd + (lane)] = s.M[(r) * kNodeLd + (src)];
         d.C[lane] = (lane < ncol - 1) ? s.C[src] : T(0);
         d.var[lane] = s.var[src];
     }
     __syncwarp();
     for (int j = 0; j + 1 < p; ++j) {
-        const T a = d.M[j][j], b = d.M[j + 1][j];
+        const T a = d.M[(j) * kNodeLd + (j)], b = d.M[(j + 1) * kNodeLd + (j)];
         T c, sn, rho;
         givens(a, b, c, sn, rho);
         T x = T(0), y = T(0);
         if (lane < ncol) {
-            x = d.M[j][lane];
-            y = d.M[j + 1][lane];
+            x = d.M[(j) * kNodeLd + (lane)];
+            y = d.M[(j + 1) * kNodeLd + (lane)];
         }
         __syncwarp();
         if (lane < ncol) {
@@ -98,17 +107,17 @@ __device__ void node_exclude(const Node<T>& s, Node<T>& d, int lane) {
                 nx = rho;
                 ny = T(0);
             }
-            d.M[j][lane] = nx;
-            d.M[j + 1][lane] = ny;
+            d.M[(j) * kNodeLd + (lane)] = nx;
+            d.M[(j + 1) * kNodeLd + (lane)] = ny;
         }
         __syncwarp();
     }
     if (lane < ncol) {
         if (lane >= p - 1) {
-            const T y = d.M[p - 1][lane];
+            const T y = d.M[(p - 1) * kNodeLd + (lane)];
             d.C[lane] += y * y;
         }
-        d.M[p - 1][lane] = T(0);
+        d.M[(p - 1) * kNodeLd + (lane)] = T(0);
     }
     if (lane == 0) {
         d.p = p - 1;
@@ -118,34 +127,40 @@ __device__ void node_exclude(const Node<T>& s, Node<T>& d, int lane) {
 }
 
 template <typename T>
-__device__ void write_leaf(const Node<T>& nd, int ell, int Q, T* rec, int lane) {
+__device__ void write_leaf(const Node<T>& nd, int ell, int Q, T* rec, int lane, size_t stride,
+                           unsigned long long* chk) {
     const int LQ = Q * (Q + 1) / 2;
     for (int e = lane; e < LQ; e += 32) {
         int pc = 0;
         while ((pc + 1) * (pc + 2) / 2 <= e) ++pc;
         const int r = e - pc * (pc + 1) / 2;
-        rec[(size_t)e * 32 + ell] = nd.M[r][pc];
+        if (GBN_IN(chk, 221, (size_t)e * 32 + ell, stride) && GBN_IN(chk, 222, r * 32 + pc, 1024))
+            rec[(size_t)e * 32 + ell] = nd.M[(r) * kNodeLd + (pc)];
     }
     const int nc = nd.nc;
     for (int e = lane; e < nc * (Q + 1); e += 32) {
         const int col = Q + e / (Q + 1), row = e % (Q + 1);
+        if (!GBN_IN(chk, 223, col, 32)) continue;
         const int v = nd.var[col];
-        const T val = (row < Q) ? nd.M[row][col] : nd.C[col];
-        rec[(size_t)(LQ + v * (Q + 1) + row) * 32 + ell] = val;
+        const T val = (row < Q) ? nd.M[(row) * kNodeLd + (col)] : nd.C[col];
+        if (GBN_IN(chk, 224, (size_t)(LQ + v * (Q + 1) + row) * 32 + ell, stride))
+            rec[(size_t)(LQ + v * (Q + 1) + row) * 32 + ell] = val;
     }
     __syncwarp();
 }
 
 template <typename T>
 __global__ void __launch_bounds__(32) roots_kernel(const double* __restrict__ R0, Plan p,
-                                                   T* __restrict__ leaves) {
+                                                   T* __restrict__ leaves,
+                                                   unsigned long long* chk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Node<T>* nodes = reinterpret_cast<Node<T>*>(smem_raw);
     const int lane = threadIdx.x;
     const int m = p.m;
     Node<T>& n0 = nodes[0];
     if (lane < m) {
-        for (int r = 0; r < m; ++r) n0.M[r][lane] = (T)R0[r * m + lane];
+        for (int r = 0; r < m; ++r)
+            if (GBN_IN(chk, 231, r * 32 + lane, 1024)) n0.M[(r) * kNodeLd + (lane)] = (T)R0[r * m + lane];
         n0.C[lane] = T(0);
         n0.var[lane] = p.order[lane];
     }
@@ -158,9 +173,9 @@ __global__ void __launch_bounds__(32) roots_kernel(const double* __restrict__ R0
     int cur = 0;
     for (int j = 0; j < p.k - p.W; ++j) {
         if ((cta >> j) & 1ull)
-            node_include(nodes[cur], nodes[cur ^ 1], lane);
+            node_include(nodes[cur], nodes[cur ^ 1], lane, chk);
         else
-            node_exclude(nodes[cur], nodes[cur ^ 1], lane);
+            node_exclude(nodes[cur], nodes[cur ^ 1], lane, chk);
         cur ^= 1;
     }
     T* rec = leaves + (size_t)blockIdx.x * p.leaf_stride;
@@ -173,11 +188,11 @@ __global__ void __launch_bounds__(32) roots_kernel(const double* __restrict__ R0
         const int t0 = (lam == 0) ? 0 : __ffs(ell ^ prev) - 1;
         for (int t = t0; t < p.W; ++t) {
             if ((ell >> t) & 1)
-                node_include(*lvl[t], *lvl[t + 1], lane);
+                node_include(*lvl[t], *lvl[t + 1], lane, chk);
             else
-                node_exclude(*lvl[t], *lvl[t + 1], lane);
+                node_exclude(*lvl[t], *lvl[t + 1], lane, chk);
         }
-        write_leaf(*lvl[p.W], ell, p.Q, rec, lane);
+        write_leaf(*lvl[p.W], ell, p.Q, rec, lane, p.leaf_stride, chk);
         prev = ell;
     }
 }
@@ -186,6 +201,7 @@ template <typename T>
 int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
     const double* r0 = reinterpret_cast<const double*>(ws + p.off_r0);
     T* leaves = reinterpret_cast<T*>(ws + p.off_leaves);
+    unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
     const size_t smem = sizeof(Node<T>) * (size_t)(p.W + 2);
     static bool attr_set = false;
     if (!attr_set) {
@@ -194,7 +210,7 @@ int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
             return GBN_ERR_CUDA;
         attr_set = true;
     }
-    roots_kernel<T><<<(unsigned)p.n_cta, 32, smem, stream>>>(r0, p, leaves);
+    roots_kernel<T><<<(unsigned)p.n_cta, 32, smem, stream>>>(r0, p, leaves, chk);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 

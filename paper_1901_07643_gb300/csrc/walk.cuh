@@ -60,6 +60,8 @@ struct WalkArgs {
     T alpha;  // n ln 2
     T lnn;    // ln n
     T nlnn;   // n ln n
+    unsigned long long* chk;  // check record (checked builds)
+    size_t out_size;          // table elements
 };
 
 __device__ __forceinline__ float wk_rsqrt(float x) { return rsqrtf(x); }
@@ -79,7 +81,10 @@ __device__ __forceinline__ void for_steps(std::index_sequence<Ts...>, F&& f) {
 }
 
 template <typename T, bool COV>
-__device__ __forceinline__ void emit(void* out, size_t idx, T rss, T alpha, T pen) {
+__device__ __forceinline__ void emit(const WalkArgs<T>& a, size_t idx, T rss, T pen) {
+    if (!GBN_IN(a.chk, 301, idx, a.out_size)) return;
+    void* out = a.out;
+    const T alpha = a.alpha;
     if constexpr (COV) {
         atomicAdd(reinterpret_cast<unsigned*>(out) + idx, 1u);
     } else {
@@ -93,19 +98,25 @@ template <typename T, int Q, bool COV>
 __device__ __forceinline__ void l_walk(const WalkArgs<T>& a, const T* __restrict__ rec,
                                        typename Vec2T<T>::type* tape, int lane, uint64_t F) {
     constexpr int N = WalkSeq<Q>::N;
-    T R[Q][Q];      // R[row][position], rows <= position
-    T Wt[Q + 1][Q]; // Wt[r][p] = sum_{t=r..p} R[t][p]^2
+    // Register arrays, flat and indexed only by compile-time constants:
+    // R[row * Q + position] (rows <= position) and
+    // Wt[r * Q + p] = sum_{t=r..p} R[(t) * Q + (p)]^2.
+    T R[Q * Q];
+    T Wt[(Q + 1) * Q];
 #pragma unroll
     for (int pc = 0; pc < Q; ++pc)
 #pragma unroll
-        for (int r = 0; r <= pc; ++r) R[r][pc] = rec[(size_t)(pc * (pc + 1) / 2 + r) * 32 + lane];
+        for (int r = 0; r <= pc; ++r)
+            R[(r) * Q + (pc)] = GBN_IN(a.chk, 302, (size_t)(pc * (pc + 1) / 2 + r) * 32 + lane, a.leaf_stride)
+                           ? rec[(size_t)(pc * (pc + 1) / 2 + r) * 32 + lane]
+                           : T(0);
 #pragma unroll
     for (int pc = 0; pc < Q; ++pc) {
         T acc = T(0);
 #pragma unroll
         for (int r = pc; r >= 0; --r) {
-            acc = fma(R[r][pc], R[r][pc], acc);
-            Wt[r][pc] = acc;
+            acc = fma(R[(r) * Q + (pc)], R[(r) * Q + (pc)], acc);
+            Wt[(r) * Q + (pc)] = acc;
         }
     }
     const int dF = __popcll(F);
@@ -120,52 +131,52 @@ __device__ __forceinline__ void l_walk(const WalkArgs<T>& a, const T* __restrict
     for (int s = 0; s < Q; ++s)
 #pragma unroll
         for (int pc = s; pc < Q; ++pc)
-            emit<T, COV>(a.out, base + (size_t)pc * cstride + ((size_t)((1u << s) - 1u) << ksh),
-                         Wt[s][pc], a.alpha, pen[s]);
+            emit<T, COV>(a, base + (size_t)pc * cstride + ((size_t)((1u << s) - 1u) << ksh),
+                         Wt[(s) * Q + (pc)], pen[s]);
     for_steps(std::make_index_sequence<N>{}, [&](auto tc) {
         constexpr int t = decltype(tc)::value;
         constexpr int i = kWalkSeq<Q>.idx[t] - 1;  // rows i, i+1 (0-based)
-        const T x0 = R[i][i + 1], y0 = R[i + 1][i + 1];
+        const T x0 = R[(i) * Q + (i + 1)], y0 = R[(i + 1) * Q + (i + 1)];
         const T rho2 = fma(x0, x0, y0 * y0);
         const T inv = wk_rsqrt(rho2);
         const bool ok = rho2 > T(0);
         const T c = ok ? x0 * inv : T(1);
         const T s = ok ? y0 * inv : T(0);
         const T rho = ok ? rho2 * inv : T(0);
-        const T rii = R[i][i];
+        const T rii = R[(i) * Q + (i)];
         // transpose positions i, i+1 (renaming of the rows above i)
 #pragma unroll
         for (int r = 0; r < i; ++r) {
-            const T tmp = R[r][i];
-            R[r][i] = R[r][i + 1];
-            R[r][i + 1] = tmp;
+            const T tmp = R[(r) * Q + (i)];
+            R[(r) * Q + (i)] = R[(r) * Q + (i + 1)];
+            R[(r) * Q + (i + 1)] = tmp;
         }
 #pragma unroll
         for (int r = 0; r <= i; ++r) {
-            const T tmp = Wt[r][i];
-            Wt[r][i] = Wt[r][i + 1];
-            Wt[r][i + 1] = tmp;
+            const T tmp = Wt[(r) * Q + (i)];
+            Wt[(r) * Q + (i)] = Wt[(r) * Q + (i + 1)];
+            Wt[(r) * Q + (i + 1)] = tmp;
         }
-        R[i][i] = rho;
-        R[i][i + 1] = c * rii;
-        R[i + 1][i + 1] = -s * rii;
-        Wt[i + 1][i + 1] = R[i + 1][i + 1] * R[i + 1][i + 1];
+        R[(i) * Q + (i)] = rho;
+        R[(i) * Q + (i + 1)] = c * rii;
+        R[(i + 1) * Q + (i + 1)] = -s * rii;
+        Wt[(i + 1) * Q + (i + 1)] = R[(i + 1) * Q + (i + 1)] * R[(i + 1) * Q + (i + 1)];
 #pragma unroll
         for (int pc = i + 2; pc < Q; ++pc) {
-            const T x = R[i][pc], y = R[i + 1][pc];
-            R[i][pc] = fma(c, x, s * y);
-            R[i + 1][pc] = fma(c, y, -s * x);
-            Wt[i + 1][pc] = fma(R[i + 1][pc], R[i + 1][pc], Wt[i + 2][pc]);
+            const T x = R[(i) * Q + (pc)], y = R[(i + 1) * Q + (pc)];
+            R[(i) * Q + (pc)] = fma(c, x, s * y);
+            R[(i + 1) * Q + (pc)] = fma(c, y, -s * x);
+            Wt[(i + 1) * Q + (pc)] = fma(R[(i + 1) * Q + (pc)], R[(i + 1) * Q + (pc)], Wt[(i + 2) * Q + (pc)]);
         }
-        tape[t * 32 + lane] = wk_pair(c, s);
+        if (GBN_IN(a.chk, 303, t * 32 + lane, N * 32)) tape[t * 32 + lane] = wk_pair(c, s);
         constexpr unsigned pre = kWalkSeq<Q>.prefix[t];
         for_steps(std::make_index_sequence<Q>{}, [&](auto pcc) {
             constexpr int pc = decltype(pcc)::value;
             if constexpr (pc > i) {
                 constexpr int j = kWalkSeq<Q>.var_at[t][pc];
                 constexpr unsigned cT = compress_bit(pre, j);
-                emit<T, COV>(a.out, base + (size_t)j * cstride + ((size_t)cT << ksh),
-                             Wt[i + 1][pc], a.alpha, pen[i + 1]);
+                emit<T, COV>(a, base + (size_t)j * cstride + ((size_t)cT << ksh),
+                             Wt[(i + 1) * Q + (pc)], pen[i + 1]);
             }
         });
     });
@@ -183,8 +194,13 @@ __device__ __forceinline__ void b_walk(const WalkArgs<T>& a, const T* __restrict
     T z[Q];
     T w[Q + 1];
 #pragma unroll
-    for (int e = 0; e < Q; ++e) z[e] = bv[(size_t)e * 32 + ell];
-    w[Q] = bv[(size_t)Q * 32 + ell];
+    for (int e = 0; e < Q; ++e)
+        z[e] = GBN_IN(a.chk, 304, (size_t)32 * (LQ + v * (Q + 1)) + e * 32 + ell, a.leaf_stride)
+                   ? bv[(size_t)e * 32 + ell]
+                   : T(0);
+    w[Q] = GBN_IN(a.chk, 305, (size_t)32 * (LQ + v * (Q + 1)) + Q * 32 + ell, a.leaf_stride)
+               ? bv[(size_t)Q * 32 + ell]
+               : T(0);
 #pragma unroll
     for (int r = Q - 1; r >= 0; --r) w[r] = fma(z[r], z[r], w[r + 1]);
     const int dF = __popcll(F);
@@ -197,17 +213,18 @@ __device__ __forceinline__ void b_walk(const WalkArgs<T>& a, const T* __restrict
     const int ksh = a.k - 1;
 #pragma unroll
     for (int s = 0; s <= Q; ++s)
-        emit<T, COV>(a.out, base + ((size_t)((1u << s) - 1u) << ksh), w[s], a.alpha, pen[s]);
+        emit<T, COV>(a, base + ((size_t)((1u << s) - 1u) << ksh), w[s], pen[s]);
     for_steps(std::make_index_sequence<N>{}, [&](auto tc) {
         constexpr int t = decltype(tc)::value;
         constexpr int i = kWalkSeq<Q>.idx[t] - 1;
-        const auto cs = tape[t * 32 + ell];
+        typename Vec2T<T>::type cs{};
+        if (GBN_IN(a.chk, 306, t * 32 + ell, N * 32)) cs = tape[t * 32 + ell];
         const T x = z[i], y = z[i + 1];
         z[i] = fma(cs.x, x, cs.y * y);
         z[i + 1] = fma(cs.x, y, -cs.y * x);
         w[i + 1] = fma(z[i + 1], z[i + 1], w[i + 2]);
         constexpr unsigned pre = kWalkSeq<Q>.prefix[t];
-        emit<T, COV>(a.out, base + ((size_t)pre << ksh), w[i + 1], a.alpha, pen[i + 1]);
+        emit<T, COV>(a, base + ((size_t)pre << ksh), w[i + 1], pen[i + 1]);
     });
 }
 

@@ -33,6 +33,8 @@ static WalkArgs<T> walk_args(const Plan& p, char* ws, void* out) {
     a.alpha = (T)(n * 0.69314718055994530942);
     a.lnn = (T)log(n);
     a.nlnn = (T)(n * log(n));
+    a.chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
+    a.out_size = (size_t)p.m << (p.m - 1);
     return a;
 }
 
