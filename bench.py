@@ -45,7 +45,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="m26", choices=["m26", "m20", "m10"])
+    ap.add_argument("--workload", default="m26", choices=["m26", "m24", "m20", "m10"])
     ap.add_argument("--q", type=int, default=0)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
@@ -56,7 +56,7 @@ def _args():
 
 def _workload(name):
     from paper_1901_07643_gb300 import synthetic
-    return {"m26": synthetic.LARGE_M26, "m20": synthetic.MEDIUM_M20,
+    return {"m26": synthetic.LARGE_M26, "m24": synthetic.PROFILE_M24, "m20": synthetic.MEDIUM_M20,
             "m10": synthetic.SMALL_M10}[name]
 
 

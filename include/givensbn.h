@@ -60,6 +60,7 @@ extern "C" {
 
 /* device status bits (givensbn_status) */
 #define GBN_STATUS_RANK_DEFICIENT 1 /* a Cholesky pivot was <= 0: RSS 0 for some families */
+#define GBN_STATUS_WATCHDOG 2       /* a bounded wait inside a kernel expired: output incomplete */
 
 #define GBN_MIN_M 2
 #define GBN_MAX_M 30

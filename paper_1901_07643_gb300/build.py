@@ -20,13 +20,16 @@ LIB = os.path.join(HERE, "lib", "libgivensbn.so")
 # checked variant: every computed index bounds-checked, synchronised per stage
 OBJ_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(HERE, "lib", "libgivensbn_checked.so")
+# timing variant: per-role cycle counters in the workspace status block
+OBJ_TIMING = os.path.join(HERE, "_build_timing")
+LIB_TIMING = os.path.join(HERE, "lib", "libgivensbn_timing.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo",
                      "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
 # (scalar type, Q) pairs the dispatcher references
-WALK_INSTANCES = [("float", q) for q in range(2, 9)] + [("double", q) for q in range(2, 8)]
+WALK_INSTANCES = [("float", q) for q in range(2, 13)] + [("double", q) for q in range(2, 9)]
 
 
 def _nvcc() -> str:
@@ -58,9 +61,14 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, jobs: int = 0, verbose: bool = False, checked: bool = False) -> str:
-    obj_dir, lib = (OBJ_CHECKED, LIB_CHECKED) if checked else (OBJ, LIB)
-    extra = ["-DGBN_CHECKED"] if checked else []
+def build(force: bool = False, jobs: int = 0, verbose: bool = False, checked: bool = False,
+          timing: bool = False) -> str:
+    if checked:
+        obj_dir, lib, extra = OBJ_CHECKED, LIB_CHECKED, ["-DGBN_CHECKED"]
+    elif timing:
+        obj_dir, lib, extra = OBJ_TIMING, LIB_TIMING, ["-DGBN_TIMING"]
+    else:
+        obj_dir, lib, extra = OBJ, LIB, []
     os.makedirs(obj_dir, exist_ok=True)
     os.makedirs(os.path.dirname(lib), exist_ok=True)
     nvcc = _nvcc()
@@ -81,7 +89,6 @@ def build(force: bool = False, jobs: int = 0, verbose: bool = False, checked: bo
     if todo:
         workers = jobs or max(1, os.cpu_count() or 1)
         # largest instantiations first so the pool finishes together
-        todo.sort(key=lambda j: -(("q8" in j[0]) * 4 + ("q7" in j[0]) * 3 + ("q6" in j[0]) * 2))
         with cf.ThreadPoolExecutor(max_workers=workers) as ex:
             for obj in ex.map(run, todo):
                 if verbose:
@@ -102,6 +109,7 @@ if __name__ == "__main__":
     ap.add_argument("--force", action="store_true")
     ap.add_argument("--jobs", type=int, default=0)
     ap.add_argument("--checked", action="store_true")
+    ap.add_argument("--timing", action="store_true")
     a = ap.parse_args()
-    build(force=a.force, jobs=a.jobs, verbose=True, checked=a.checked)
+    build(force=a.force, jobs=a.jobs, verbose=True, checked=a.checked, timing=a.timing)
     sys.exit(0)

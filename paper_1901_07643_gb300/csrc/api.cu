@@ -9,14 +9,15 @@ namespace gbn {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-static int max_q(int precision) { return precision ? 7 : kMaxQ; }
+static int max_q(int precision) { return precision ? kMaxQFp64 : kMaxQ; }
 
 int auto_q(int m, int precision) {
-    // Enough CTAs (2^(m-Q-5)) to fill the GPU several times over once m is
-    // large, and never more free variables than the register-resident block
-    // and the shared-memory tape hold.
-    int q = m - 14;
-    if (q < 4) q = 4;
+    // Large sub-walks amortise their roots; keep 2^(m-Q-5) CTAs >= ~4000 so
+    // that every SM gets a couple of dozen sub-walk tiles once m is large.
+    (void)precision;
+    int q = m - 17;
+    if (q < 6) q = 6;
+    if (q > 9) q = 9;
     if (q > max_q(precision)) q = max_q(precision);
     if (q > m) q = m;
     return q;
@@ -51,6 +52,14 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     p->coverage = opts ? (opts->debug_coverage != 0) : 0;
     const size_t es = precision ? sizeof(double) : sizeof(float);
     p->leaf_stride = leaf_stride_elems(Q, p->k);
+    {  // consumer warps: the fixed variables above the lowest W, then the lowest W
+        const int g = p->W >= 1 ? (p->lanes >> 1) : 1;
+        const int n5 = p->W >= 1 ? (p->W + (32 / g) - 1) / (32 / g) : 0;
+        const int uw = (p->k - p->W + kConsumerSlots - 1) / kConsumerSlots;
+        const int lw = (n5 + kConsumerSlots - 1) / kConsumerSlots;
+        p->n_bwarps = uw + lw < 1 ? 1 : uw + lw;
+        if (p->n_bwarps > 8) return GBN_ERR_Q;
+    }
     size_t off = 0;
     p->off_status = off;
     off = align_up(off + 256, 256);

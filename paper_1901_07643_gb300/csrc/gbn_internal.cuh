@@ -29,10 +29,13 @@ __device__ __forceinline__ bool gbn_in_bounds(unsigned long long* rec, int site,
 
 namespace gbn {
 
-constexpr int kCheckOffset = 64;  // byte offset of the check record in the status block
+constexpr int kCheckOffset = 64;    // byte offset of the check record in the status block
+constexpr int kTimingOffset = 128;  // byte offset of the timing counters (timing builds)
 
-constexpr int kMaxQ = 8;     // largest sub-walk size compiled
+constexpr int kMaxQ = 12;    // largest sub-walk size compiled (FP32)
+constexpr int kMaxQFp64 = 8; // FP64: the register-resident block is twice as large
 constexpr int kMinQ = 2;
+constexpr int kConsumerSlots = 4;  // fixed variables carried per consumer thread
 constexpr int kLaneBits = 5; // sub-walks per warp = 2^kLaneBits (one per lane)
 
 // Row-panel count for the tall-skinny passes over X.
@@ -57,6 +60,7 @@ struct Plan {
     size_t off_status = 0, off_colsum = 0, off_gram = 0, off_r1 = 0, off_r0 = 0, off_leaves = 0;
     size_t total_bytes = 0;
     size_t leaf_stride = 0;  // elements per CTA leaf record
+    int n_bwarps = 1;        // consumer warps per walk CTA
 };
 
 int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* plan);
@@ -74,52 +78,5 @@ int launch_walk(const Plan& p, char* ws, void* out, cudaStream_t stream);
 inline size_t leaf_stride_elems(int Q, int k) {
     return (size_t)32 * ((size_t)Q * (Q + 1) / 2 + (size_t)k * (Q + 1));
 }
-
-// ---------------------------------------------------------------------------
-// The greedy transposition sequence of Algorithm 1 (GreedySwaps), generated at
-// compile time for a sub-walk of Q variables, plus what every step reads out.
-// Positions and swap indices are 1-based as in the paper; the stored tables
-// use 0-based positions.
-template <int Q>
-struct WalkSeq {
-    static constexpr int N = (1 << Q) - Q - 1;  // |Upsilon(Q)|, Sec. 3
-    int idx[N > 0 ? N : 1];                     // swap index i (1-based) of step t
-    unsigned prefix[N > 0 ? N : 1];             // local variables at positions 1..i after step t
-    int var_at[N > 0 ? N : 1][Q];               // local variable at each position after step t
-};
-
-template <int Q>
-constexpr WalkSeq<Q> make_walk_seq() {
-    WalkSeq<Q> s{};
-    int buf[(1 << Q) + 1] = {};
-    int len = 0;
-    if (Q >= 2) {
-        buf[0] = 1;  // Upsilon(2) = [1]
-        len = 1;
-    }
-    // Upsilon(j+1) = Upsilon(j) : [j .. 1] : (Upsilon(j) + 1)   (Sec. 3, Sec. 5)
-    for (int j = 2; j < Q; ++j) {
-        const int old = len;
-        for (int i = j; i >= 1; --i) buf[len++] = i;
-        for (int t = 0; t < old; ++t) buf[len++] = buf[t] + 1;
-    }
-    int pos[Q > 0 ? Q : 1] = {};
-    for (int p = 0; p < Q; ++p) pos[p] = p;
-    for (int t = 0; t < len; ++t) {
-        const int i = buf[t];
-        const int tmp = pos[i - 1];
-        pos[i - 1] = pos[i];
-        pos[i] = tmp;
-        s.idx[t] = i;
-        unsigned mask = 0;
-        for (int p = 0; p < i; ++p) mask |= 1u << pos[p];
-        s.prefix[t] = mask;
-        for (int p = 0; p < Q; ++p) s.var_at[t][p] = pos[p];
-    }
-    return s;
-}
-
-template <int Q>
-inline constexpr WalkSeq<Q> kWalkSeq = make_walk_seq<Q>();
 
 }  // namespace gbn

@@ -67,6 +67,7 @@ class Workload:
 # The single-instance workloads, named by what they are.
 SMALL_M10 = Workload("sem_m10_n200", 10, 200, 0.3, 1000)
 MEDIUM_M20 = Workload("sem_m20_n1000", 20, 1000, 0.2, 2000)
+PROFILE_M24 = Workload("sem_m24_n2000", 24, 2000, 0.15, 2400)
 LARGE_M26 = Workload("sem_m26_n5000_collinear2", 26, 5000, 0.15, 3000,
                      collinear=int(math.ceil(0.05 * 26)))
 

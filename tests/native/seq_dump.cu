@@ -1,20 +1,18 @@
-// Prints the compile-time swap tables the CUDA walk is built from, so that a
-// CPU test can compare them with the oracle's GreedySwaps.  Host code only.
+// Prints the compile-time swap table the CUDA walk is built from, so that a
+// CPU test can compare it with the oracle's GreedySwaps.  Host code only.
 #include <cstdio>
 
-#include "../../paper_1901_07643_gb300/csrc/gbn_internal.cuh"
+#include "../../paper_1901_07643_gb300/csrc/walk2.cuh"
 
 template <int Q>
 void dump() {
-    constexpr auto& s = gbn::kWalkSeq<Q>;
-    for (int t = 0; t < gbn::WalkSeq<Q>::N; ++t) {
-        std::printf("%d %d %u", Q, s.idx[t], s.prefix[t]);
-        for (int p = 0; p < Q; ++p) std::printf(" %d", s.var_at[t][p]);
-        std::printf("\n");
-    }
+    constexpr auto tab = gbn::make_step_tab<Q>();
+    for (int t = 0; t < gbn::StepTab<Q>::N; ++t)
+        std::printf("%d %u %u\n", Q, (tab.e[t] & 15u) + 1u, tab.e[t] >> 4);
 }
 
 int main() {
     dump<2>(); dump<3>(); dump<4>(); dump<5>(); dump<6>(); dump<7>(); dump<8>();
+    dump<9>(); dump<10>(); dump<11>(); dump<12>();
     return 0;
 }

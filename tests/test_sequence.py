@@ -147,3 +147,16 @@ def test_split_swap_counts():
             _, sw = seq.seed_path(bits, m)
             assert len(sw) == 2 ** (m - k) - (m - k) - 1
             assert min(sw) == sum(bits) + 1 and max(sw) == sum(bits) + m - k - 1
+
+
+@pytest.mark.parametrize("m", range(2, 17))
+def test_consecutive_swaps_are_adjacent(m):
+    """Upsilon(m) starts at index 1, ends at m-1 and moves by exactly one per step.
+
+    Induction on the recursion of Sec. 3: Upsilon(m-1) ends at m-2, the chain
+    [m-1 .. 1] starts at m-1 and ends at 1, and Upsilon(m-1)+1 starts at 2.
+    The CUDA walk relies on this to branch directly between row blocks.
+    """
+    sw = seq.greedy_swaps(m)
+    assert sw[0] == 1 and sw[-1] == m - 1
+    assert all(abs(a - b) == 1 for a, b in zip(sw, sw[1:]))
