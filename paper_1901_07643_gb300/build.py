@@ -29,7 +29,7 @@ NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-lineinfo
                      "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
 # (scalar type, Q) pairs the dispatcher references
-WALK_INSTANCES = [("float", q) for q in range(2, 13)] + [("double", q) for q in range(2, 9)]
+WALK_INSTANCES = [("float", q) for q in range(2, 10)] + [("double", q) for q in range(2, 9)]
 
 
 def _nvcc() -> str:

@@ -12,12 +12,13 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 static int max_q(int precision) { return precision ? kMaxQFp64 : kMaxQ; }
 
 int auto_q(int m, int precision) {
-    // Large sub-walks amortise their roots; keep 2^(m-Q-5) CTAs >= ~4000 so
-    // that every SM gets a couple of dozen sub-walk tiles once m is large.
+    // Large sub-walks amortise their roots; the tape of one sub-walk tile
+    // (2^Q - Q - 1 steps) stays in shared memory, so Q <= 8 keeps several
+    // tiles resident per SM.
     (void)precision;
-    int q = m - 17;
+    int q = m - 18;
     if (q < 6) q = 6;
-    if (q > 9) q = 9;
+    if (q > 8) q = 8;
     if (q > max_q(precision)) q = max_q(precision);
     if (q > m) q = m;
     return q;
@@ -52,13 +53,13 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     p->coverage = opts ? (opts->debug_coverage != 0) : 0;
     const size_t es = precision ? sizeof(double) : sizeof(float);
     p->leaf_stride = leaf_stride_elems(Q, p->k);
-    {  // consumer warps: the fixed variables above the lowest W, then the lowest W
+    {  // consumer warps: enough that the largest CTA gives each a few columns to replay
         const int g = p->W >= 1 ? (p->lanes >> 1) : 1;
         const int n5 = p->W >= 1 ? (p->W + (32 / g) - 1) / (32 / g) : 0;
-        const int uw = (p->k - p->W + kConsumerSlots - 1) / kConsumerSlots;
-        const int lw = (n5 + kConsumerSlots - 1) / kConsumerSlots;
-        p->n_bwarps = uw + lw < 1 ? 1 : uw + lw;
-        if (p->n_bwarps > 8) return GBN_ERR_Q;
+        const int items = Q + (p->k - p->W) + n5;
+        int nw = (items + kItemsPerWarp - 1) / kItemsPerWarp;
+        if (nw > 8) nw = 8;
+        p->n_bwarps = nw < 1 ? 1 : nw;
     }
     size_t off = 0;
     p->off_status = off;

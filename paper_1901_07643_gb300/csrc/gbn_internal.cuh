@@ -32,10 +32,10 @@ namespace gbn {
 constexpr int kCheckOffset = 64;    // byte offset of the check record in the status block
 constexpr int kTimingOffset = 128;  // byte offset of the timing counters (timing builds)
 
-constexpr int kMaxQ = 12;    // largest sub-walk size compiled (FP32)
+constexpr int kMaxQ = 9;     // largest sub-walk size compiled (FP32; the tape lives in shared memory)
 constexpr int kMaxQFp64 = 8; // FP64: the register-resident block is twice as large
 constexpr int kMinQ = 2;
-constexpr int kConsumerSlots = 4;  // fixed variables carried per consumer thread
+constexpr int kItemsPerWarp = 3;  // columns each consumer warp replays, for the largest CTA
 constexpr int kLaneBits = 5; // sub-walks per warp = 2^kLaneBits (one per lane)
 
 // Row-panel count for the tall-skinny passes over X.
@@ -60,7 +60,7 @@ struct Plan {
     size_t off_status = 0, off_colsum = 0, off_gram = 0, off_r1 = 0, off_r0 = 0, off_leaves = 0;
     size_t total_bytes = 0;
     size_t leaf_stride = 0;  // elements per CTA leaf record
-    int n_bwarps = 1;        // consumer warps per walk CTA
+    int n_bwarps = 1;        // consumer warps per walk CTA (they loop over the CTA's columns)
 };
 
 int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* plan);

@@ -1,0 +1,507 @@
+// The Givens walk (Sec. 1.3, Sec. 2, Algorithm 1) over the sub-walks of one CTA.
+//
+// Each CTA owns 2^W sub-walks that share their front variables above the
+// lowest W fixed variables and differ in those W (lane l of a warp <-> the
+// sub-walk whose front set holds fixed variable b iff bit b of l is set).  All
+// sub-walks run the same local sequence Upsilon(Q), so the swap row of every
+// step and the prefix set after it are compile-time constants.
+//
+// Warp 0 (producer) walks, per lane, the Q x Q block of R over the free
+// variables with registers named by column position and writes the rotation
+// of every step to a tape in shared memory: cos = r_{i,i+1}/rho and
+// sin = r_{i+1,i+1}/rho, the rotation of the GRC operator that zeroes the
+// sub-diagonal (the paper prints the same numerator for both).  The swap rows
+// move by exactly one per step (Algorithm 1 joins its parts at rows that
+// differ by one), so the producer is a state machine with one straight-line
+// block per row and a direct branch to the row above or below: its code size
+// is O(Q^2), whatever the 2^Q - Q - 1 steps.
+//
+// The other warps (consumers) take the CTA's columns one at a time and replay
+// the whole tape over each with straight-line code unrolled over the steps:
+//   * free variable j: its column of the root block;  it is a child whenever
+//     j is behind the prefix;
+//   * fixed variable v outside the front set: its Q entries in the free
+//     block's rows plus the residual C below them; a child of every prefix.
+// A column is a Q-vector z with tail sums w[r] = sum_{t>=r} z_t^2 + C, the RSS
+// of the column on the variables in positions < r.  A swap at row i rotates
+// rows i, i+1 of z (rows ahead of the column's position are zero and stay
+// zero) and changes only w[i+1] = w[i+2] + z_{i+1}^2; the families it adds are
+// those whose parent set is the new prefix of length i+1 (Sec. 4).
+//
+// The tape is written in chunks; each chunk has an mbarrier the producer
+// arrives on, so consumers start on the first chunk while the producer walks
+// on.  Every wait is bounded by a wall-clock watchdog that records
+// GBN_STATUS_WATCHDOG and returns.
+//
+// Scores: score = n ln(RSS/n) + |S| ln n = (n ln 2) log2(RSS) + (|S| ln n - n ln n),
+// stored at idx(c,S) = c 2^(m-1) + compress(S, c); the lanes of a warp write
+// consecutive table slots.
+#pragma once
+
+#include <type_traits>
+#include <utility>
+
+#include "gbn_internal.cuh"
+
+namespace gbn {
+
+template <typename T>
+struct Vec2T;
+template <>
+struct Vec2T<float> {
+    using type = float2;
+};
+template <>
+struct Vec2T<double> {
+    using type = double2;
+};
+
+template <typename T>
+struct WalkArgs {
+    void* out;
+    const T* leaves;
+    size_t leaf_stride;
+    int m, k, W, lanes;
+    T alpha;                     // n ln 2
+    T lnn;                       // ln n
+    T nlnn;                      // n ln n
+    unsigned long long* chk;     // check record (checked builds)
+    unsigned long long* timing;  // role cycle counters (timing builds)
+    int* status;                 // status word (watchdog bit)
+    size_t out_size;             // table elements
+    int n_cwarps;                // consumer warps per CTA
+    long long watchdog_ns;       // bound on every wait
+};
+
+constexpr int kChunk = 16;  // tape steps per barrier
+
+// The swap sequence of Algorithm 1 with, per step, the 0-based swap row i
+// (the paper's GRC_{i+1}) and the mask of the local free variables at
+// positions 0..i after the swap.
+template <int Q>
+struct StepTab {
+    static constexpr int N = (1 << Q) - Q - 1;  // |Upsilon(Q)|, Sec. 3
+    uint8_t row[N > 0 ? N : 1];
+    uint16_t pre[N > 0 ? N : 1];
+};
+
+template <int Q>
+constexpr StepTab<Q> make_step_tab() {
+    StepTab<Q> tab{};
+    int buf[(1 << Q) + 1] = {};
+    int len = 0;
+    if (Q >= 2) {
+        buf[0] = 1;  // Upsilon(2) = [1]
+        len = 1;
+    }
+    // Upsilon(j+1) = Upsilon(j) : [j .. 1] : (Upsilon(j) + 1)   (Sec. 3, Sec. 5)
+    for (int j = 2; j < Q; ++j) {
+        const int old = len;
+        for (int i = j; i >= 1; --i) buf[len++] = i;
+        for (int t = 0; t < old; ++t) buf[len++] = buf[t] + 1;
+    }
+    int pos[Q > 0 ? Q : 1] = {};
+    for (int p = 0; p < Q; ++p) pos[p] = p;
+    for (int t = 0; t < len; ++t) {
+        const int i = buf[t];
+        const int tmp = pos[i - 1];
+        pos[i - 1] = pos[i];
+        pos[i] = tmp;
+        unsigned mask = 0;
+        for (int p = 0; p < i; ++p) mask |= 1u << pos[p];
+        tab.row[t] = (uint8_t)(i - 1);
+        tab.pre[t] = (uint16_t)mask;
+    }
+    return tab;
+}
+
+template <int Q>
+inline constexpr StepTab<Q> kSteps = make_step_tab<Q>();
+
+__device__ __forceinline__ float wk_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double wk_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float wk_log2(float x) { return __log2f(x); }
+__device__ __forceinline__ double wk_log2(double x) { return log2(x); }
+__device__ __forceinline__ float2 wk_pair(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 wk_pair(double a, double b) { return make_double2(a, b); }
+
+// Element type of the output table: scores, or 32-bit counters in coverage mode.
+template <typename T, bool COV>
+using OutT = typename std::conditional<COV, unsigned, T>::type;
+
+// Store at p + off (p: a per-thread pointer into the table, off < 2^32) when
+// `on`.  The score is computed unconditionally; only the store is predicated.
+template <typename T, bool COV>
+__device__ __forceinline__ void emit_ptr(const WalkArgs<T>& a, OutT<T, COV>* p, uint32_t off,
+                                         T rss, T pen, bool on) {
+    if constexpr (COV) {
+        if (on && GBN_IN(a.chk, 302,
+                         (size_t)(p - reinterpret_cast<OutT<T, COV>*>(a.out)) + off, a.out_size))
+            atomicAdd(p + off, 1u);
+    } else {
+        const T v = fma(a.alpha, wk_log2(rss), pen);
+        if (on && GBN_IN(a.chk, 302,
+                         (size_t)(p - reinterpret_cast<OutT<T, COV>*>(a.out)) + off, a.out_size))
+            p[off] = v;
+    }
+}
+
+// ---------------------------------------------------------------- mbarriers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+            smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the phase with the given parity; false = watchdog expired.
+// try_wait suspends the thread for a short hardware-defined time when the
+// phase is not complete; the clock is read only every 64 polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit_ns,
+                                          int* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = global_ns();
+    for (unsigned n = 1;; ++n) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((n & 63u) == 0) {
+            if (global_ns() - t0 > limit_ns) {
+                atomicOr(status, GBN_STATUS_WATCHDOG);
+                return false;
+            }
+            __nanosleep(128);
+        }
+    }
+}
+// Warp-uniform form: lane 0 polls, every lane gets the same answer, and the
+// __syncwarp orders lane 0's acquire before the other lanes' later reads.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity, long long limit_ns,
+                                          int* status) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, limit_ns, status) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+
+// Timing builds (-DGBN_TIMING) add the cycles each role spends in total and
+// waiting on the tape barriers to counters in the workspace status block:
+// [0] producer total, [1] producer waiting, [2] consumer total, [3] consumer
+// waiting (summed over warps, lane 0 only).  Ordinary builds compile them away.
+#ifdef GBN_TIMING
+#define GBN_TIMER_DECL long long gbn_t_wait = 0, gbn_t_start = clock64();
+#define GBN_TIMED_WAIT(expr)                \
+    ({                                      \
+        const long long gbn_t0 = clock64(); \
+        const bool gbn_ok = (expr);         \
+        gbn_t_wait += clock64() - gbn_t0;   \
+        gbn_ok;                             \
+    })
+#define GBN_TIMER_FLUSH(ctr, slot)                                                              \
+    if ((threadIdx.x & 31) == 0) {                                                              \
+        atomicAdd((unsigned long long*)(ctr) + 2 * (slot),                                      \
+                  (unsigned long long)(clock64() - gbn_t_start));                               \
+        atomicAdd((unsigned long long*)(ctr) + 2 * (slot) + 1, (unsigned long long)gbn_t_wait); \
+    }
+#else
+#define GBN_TIMER_DECL
+#define GBN_TIMED_WAIT(expr) (expr)
+#define GBN_TIMER_FLUSH(ctr, slot)
+#endif
+
+template <int... Is, class F>
+__device__ __forceinline__ void static_for(std::integer_sequence<int, Is...>, F&& f) {
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+
+__device__ __forceinline__ int nth_zero_bit(uint64_t x, int nth) {
+    for (int b = 0; b < 64; ++b) {
+        if (!((x >> b) & 1ull)) {
+            if (nth == 0) return b;
+            --nth;
+        }
+    }
+    return 63;
+}
+
+// Shared-memory layout of one CTA: the whole tape and one barrier per chunk.
+template <typename T, int Q>
+struct Smem {
+    static constexpr int N = StepTab<Q>::N;
+    static constexpr int chunks = (N + kChunk - 1) / kChunk;
+    static constexpr size_t off_tape = 0;
+    static constexpr size_t off_bar = ((size_t)N * 32 * 2 * sizeof(T) + 15) / 16 * 16;
+    static constexpr size_t bytes = off_bar + (size_t)chunks * sizeof(uint64_t);
+};
+
+// One swap of the producer at compile-time row I.  R is named by position:
+// R[r * Q + p] (r <= p) is row r of the column at position p.
+template <typename T, int Q, int I>
+__device__ __forceinline__ void produce_step(T (&R)[Q * Q], T& c_out, T& s_out) {
+    const T x0 = R[I * Q + I + 1], y0 = R[(I + 1) * Q + I + 1];
+    const T rho2 = fma(x0, x0, y0 * y0);
+    const T inv = wk_rsqrt(rho2);
+    const bool ok = rho2 > T(0);
+    const T c = ok ? x0 * inv : T(1);
+    const T s = ok ? y0 * inv : T(0);
+    const T rii = R[I * Q + I];
+    // transpose positions I and I+1: the rows above I move with their columns
+#pragma unroll
+    for (int r = 0; r < I; ++r) {
+        const T tr = R[r * Q + I];
+        R[r * Q + I] = R[r * Q + I + 1];
+        R[r * Q + I + 1] = tr;
+    }
+    R[I * Q + I] = ok ? rho2 * inv : T(0);
+    R[I * Q + I + 1] = c * rii;
+    R[(I + 1) * Q + I + 1] = -s * rii;
+#pragma unroll
+    for (int p = I + 2; p < Q; ++p) {
+        const T x = R[I * Q + p], y = R[(I + 1) * Q + p];
+        R[I * Q + p] = fma(c, x, s * y);
+        R[(I + 1) * Q + p] = fma(c, y, -s * x);
+    }
+    c_out = c;
+    s_out = s;
+}
+
+// Producer: one sub-walk per lane over its free block, rotations only.
+template <typename T, int Q>
+__device__ __forceinline__ void produce(const WalkArgs<T>& a, const StepTab<Q>& tab,
+                                        const T* __restrict__ rec, unsigned char* smem, int lane,
+                                        bool active) {
+    using S = Smem<T, Q>;
+    using T2 = typename Vec2T<T>::type;
+    constexpr int N = StepTab<Q>::N;
+    T2* tape = reinterpret_cast<T2*>(smem + S::off_tape);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::off_bar);
+    T R[Q * Q];
+    static_for(std::make_integer_sequence<int, Q>{}, [&](auto pc) {
+        constexpr int p = decltype(pc)::value;
+        static_for(std::make_integer_sequence<int, p + 1>{}, [&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            const size_t e = (size_t)(p * (p + 1) / 2 + r) * 32 + lane;
+            R[r * Q + p] = (active && GBN_IN(a.chk, 311, e, a.leaf_stride)) ? rec[e] : T(0);
+        });
+    });
+    GBN_TIMER_DECL
+    int t = 0;
+    T c = T(1), s = T(0);
+#define GBN_PSTEP(r, UP, DOWN)                                                     \
+    if (r < Q - 1) {                                                               \
+        produce_step<T, Q, (r < Q - 1 ? r : 0)>(R, c, s);                          \
+        tape[t * 32 + lane] = wk_pair(c, s);                                       \
+        if (++t == N) goto p_done;                                                 \
+        if (t % kChunk == 0) {                                                     \
+            __syncwarp();                                                          \
+            if (lane == 0) mbar_arrive(&full[t / kChunk - 1]);                     \
+        }                                                                          \
+        if ((int)tab.row[t] > r) goto UP;                                          \
+        goto DOWN;                                                                 \
+    }
+p_r0: GBN_PSTEP(0, p_r1, p_r0)
+p_r1: GBN_PSTEP(1, p_r2, p_r0)
+p_r2: GBN_PSTEP(2, p_r3, p_r1)
+p_r3: GBN_PSTEP(3, p_r4, p_r2)
+p_r4: GBN_PSTEP(4, p_r5, p_r3)
+p_r5: GBN_PSTEP(5, p_r6, p_r4)
+p_r6: GBN_PSTEP(6, p_r7, p_r5)
+p_r7: GBN_PSTEP(7, p_r8, p_r6)
+p_r8: GBN_PSTEP(8, p_r9, p_r7)
+p_r9: GBN_PSTEP(9, p_r10, p_r8)
+p_r10: GBN_PSTEP(10, p_r10, p_r9)
+#undef GBN_PSTEP
+p_done:
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&full[(N - 1) / kChunk]);
+    GBN_TIMER_FLUSH(a.timing, 0)
+}
+
+// One column replayed from the tape with straight-line code.  jj is the bit
+// of the column's free variable in the prefix masks (Q for a fixed variable:
+// never in a prefix), sh the shift that places the compressed prefix mask in
+// the table slot.  Returns false if a wait expired.
+template <typename T, int Q, bool COV>
+__device__ __forceinline__ bool replay(const WalkArgs<T>& a, const typename Vec2T<T>::type* tape,
+                                       uint64_t* full, T (&z)[Q], T cres, int ell, int jj, int sh,
+                                       OutT<T, COV>* base, T penb, bool on) {
+    constexpr int N = StepTab<Q>::N;
+    T w[Q + 1];
+    w[Q] = cres;
+#pragma unroll
+    for (int r = Q - 1; r >= 0; --r) w[r] = fma(z[r], z[r], w[r + 1]);
+    const unsigned lm = (1u << jj) - 1u;
+    // families of the root: parents = the first s free variables
+    static_for(std::make_integer_sequence<int, Q + 1>{}, [&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        constexpr unsigned pre = (1u << s) - 1u;
+        const bool child = !((pre >> jj) & 1u);
+        const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
+        emit_ptr<T, COV>(a, base, cT << sh, w[s], fma(T(s), a.lnn, penb), on && child);
+    });
+    bool ok = true;
+    static_for(std::make_integer_sequence<int, N>{}, [&](auto tc) {
+        constexpr int t = decltype(tc)::value;
+        if constexpr (t % kChunk == 0) {
+            if (ok) ok = warp_wait(&full[t / kChunk], 0, a.watchdog_ns, a.status);
+        }
+        constexpr int i = kSteps<Q>.row[t];
+        constexpr unsigned pre = kSteps<Q>.pre[t];
+        const auto cs = tape[t * 32 + ell];
+        const T x = z[i], y = z[i + 1];
+        z[i] = fma(cs.x, x, cs.y * y);
+        const T yn = fma(cs.x, y, -cs.y * x);
+        z[i + 1] = yn;
+        const T wn = fma(yn, yn, w[i + 2]);
+        w[i + 1] = wn;
+        const bool child = !((pre >> jj) & 1u);
+        const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
+        emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, penb), on && child && ok);
+    });
+    return ok;
+}
+
+// Consumers: the CTA's columns, item it -> warp (it mod n_cwarps).
+//   items [0, Q)             free variable j = it, every lane;
+//   items [Q, Q + nu)        the fixed variables above the lowest W outside F_hi;
+//   items [Q + nu, + n5)     the lowest W variables, 32/g per item, g = 2^(W-1)
+//                            lanes each (only sub-walks without it in F).
+template <typename T, int Q, bool COV>
+__device__ __forceinline__ void consume(const WalkArgs<T>& a, const T* __restrict__ rec,
+                                        unsigned char* smem, int lane, int cw, uint64_t cta,
+                                        uint64_t Fhi) {
+    using S = Smem<T, Q>;
+    using T2 = typename Vec2T<T>::type;
+    constexpr int LQ = Q * (Q + 1) / 2;
+    const T2* tape = reinterpret_cast<const T2*>(smem + S::off_tape);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::off_bar);
+    const int nu = (a.k - a.W) - __popcll(cta);
+    const int g = a.W >= 1 ? (a.lanes >> 1) : 1;
+    const int vpi = 32 / g;
+    const int n5 = a.W >= 1 ? (a.W + vpi - 1) / vpi : 0;
+    const int nitems = Q + nu + n5;
+    GBN_TIMER_DECL
+    for (int it = cw; it < nitems; it += a.n_cwarps) {
+        T z[Q];
+        int ell = lane, jj, sh;
+        bool on;
+        OutT<T, COV>* base;
+        T cres = T(0);
+        if (it < Q) {  // free variable j: column j of the root block
+            const int j = it;
+            on = lane < a.lanes;
+#pragma unroll
+            for (int e = 0; e < Q; ++e) {
+                const size_t ix = (size_t)(j * (j + 1) / 2 + e) * 32 + lane;
+                z[e] = (on && e <= j && GBN_IN(a.chk, 323, ix, a.leaf_stride)) ? rec[ix] : T(0);
+            }
+            jj = j;
+            sh = a.k;
+            base = reinterpret_cast<OutT<T, COV>*>(a.out) + ((size_t)(a.k + j) << (a.m - 1)) +
+                   (Fhi | (uint64_t)lane);
+        } else {  // fixed variable v outside the front set
+            int v;
+            if (it < Q + nu) {
+                v = a.W + nth_zero_bit(cta, it - Q);
+                on = lane < a.lanes;
+            } else {
+                const int j = it - Q - nu;
+                const int uu = lane / g, sub = lane % g;
+                v = j * vpi + uu;
+                on = v < a.W;
+                ell = on ? ((sub & ((1 << v) - 1)) | ((sub >> v) << (v + 1))) : 0;
+                if (!on) v = 0;
+            }
+            const size_t b0 = (size_t)32 * (LQ + v * (Q + 1));
+#pragma unroll
+            for (int e = 0; e < Q; ++e) {
+                const size_t ix = b0 + e * 32 + ell;
+                z[e] = (on && GBN_IN(a.chk, 321, ix, a.leaf_stride)) ? rec[ix] : T(0);
+            }
+            {
+                const size_t ix = b0 + Q * 32 + ell;
+                cres = (on && GBN_IN(a.chk, 322, ix, a.leaf_stride)) ? rec[ix] : T(0);
+            }
+            const uint64_t F = Fhi | (uint64_t)ell;
+            const uint64_t lowmask = (1ull << v) - 1ull;
+            jj = Q;
+            sh = a.k - 1;
+            base = reinterpret_cast<OutT<T, COV>*>(a.out) + ((size_t)v << (a.m - 1)) +
+                   (size_t)((F & lowmask) | ((F >> (v + 1)) << v));
+        }
+        const T penb = fma(T(__popcll(Fhi | (uint64_t)ell)), a.lnn, -a.nlnn);
+        if (!replay<T, Q, COV>(a, tape, full, z, cres, ell, jj, sh, base, penb, on)) return;
+    }
+    GBN_TIMER_FLUSH(a.timing, 1)
+}
+
+}  // namespace gbn
+
+// The kernel exists only in the translation unit compiled for one Q
+// (walk_inst.cu with -DGBN_Q=...).
+#ifdef GBN_Q
+namespace gbn {
+
+__constant__ StepTab<GBN_Q> c_steps = make_step_tab<GBN_Q>();
+
+constexpr int kMaxConsumerWarps = 8;
+
+template <typename T, int Q, bool COV>
+__global__ void __launch_bounds__(32 * (1 + kMaxConsumerWarps)) walk_kernel(WalkArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    using S = Smem<T, Q>;
+    static_assert(Q == GBN_Q, "one Q per translation unit");
+    static_assert(Q <= 9, "the whole tape is kept in shared memory");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::off_bar);
+    if (threadIdx.x < S::chunks) mbar_init(&full[threadIdx.x], 1);
+    for (int c = threadIdx.x + blockDim.x; c < S::chunks; c += blockDim.x) mbar_init(&full[c], 1);
+    __syncthreads();
+    const uint64_t cta = blockIdx.x;
+    const uint64_t Fhi = cta << a.W;
+    const T* rec = a.leaves + (size_t)blockIdx.x * a.leaf_stride;
+    if (warp == 0)
+        produce<T, Q>(a, c_steps, rec, smem, lane, lane < a.lanes);
+    else
+        consume<T, Q, COV>(a, rec, smem, lane, warp - 1, cta, Fhi);
+}
+
+template <typename T, int Q, bool COV>
+int launch_walk_q(const WalkArgs<T>& a, int64_t n_cta, cudaStream_t stream) {
+    const size_t smem = Smem<T, Q>::bytes;
+    if (a.n_cwarps < 1 || a.n_cwarps > kMaxConsumerWarps) return GBN_ERR_Q;
+    if (cudaFuncSetAttribute(walk_kernel<T, Q, COV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return GBN_ERR_CUDA;
+    walk_kernel<T, Q, COV><<<(unsigned)n_cta, 32 * (1 + a.n_cwarps), smem, stream>>>(a);
+    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+}
+
+}  // namespace gbn
+#endif
+
+// One instantiation per (scalar type, Q, coverage), each compiled as its own
+// object from walk_inst.cu so that the build runs in parallel.
+#define GBN_WALK_INST_NAME(T, Q, COV) gbn_launch_walk_##T##_q##Q##_c##COV
+#define GBN_WALK_DECL(T, Q, COV) \
+    int GBN_WALK_INST_NAME(T, Q, COV)(const gbn::WalkArgs<T>& a, int64_t n_cta, cudaStream_t s)

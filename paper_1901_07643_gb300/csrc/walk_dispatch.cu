@@ -1,7 +1,7 @@
 // Dispatch from a plan to the compiled walk instantiation.
 #include <math.h>
 
-#include "walk2.cuh"
+#include "walk3.cuh"
 
 #define GBN_DECL_ALL(T, COV)     \
     GBN_WALK_DECL(T, 2, COV);    \
@@ -11,10 +11,7 @@
     GBN_WALK_DECL(T, 6, COV);    \
     GBN_WALK_DECL(T, 7, COV);    \
     GBN_WALK_DECL(T, 8, COV);    \
-    GBN_WALK_DECL(T, 9, COV);    \
-    GBN_WALK_DECL(T, 10, COV);   \
-    GBN_WALK_DECL(T, 11, COV);   \
-    GBN_WALK_DECL(T, 12, COV);
+    GBN_WALK_DECL(T, 9, COV);
 #define GBN_DECL_FP64(COV)       \
     GBN_WALK_DECL(double, 2, COV); \
     GBN_WALK_DECL(double, 3, COV); \
@@ -51,8 +48,7 @@ static WalkArgs<T> walk_args(const Plan& p, char* ws, void* out) {
     a.timing = reinterpret_cast<unsigned long long*>(ws + p.off_status + kTimingOffset);
     a.status = reinterpret_cast<int*>(ws + p.off_status);
     a.out_size = (size_t)p.m << (p.m - 1);
-    a.n_bwarps = p.n_bwarps;
-    a.ni = kConsumerSlots;
+    a.n_cwarps = p.n_bwarps;
     a.watchdog_ns = kWatchdogNs;
     return a;
 }
@@ -86,9 +82,6 @@ int launch_walk(const Plan& p, char* ws, void* out, cudaStream_t stream) {
         GBN_CASE(float, 7)
         GBN_CASE(float, 8)
         GBN_CASE(float, 9)
-        GBN_CASE(float, 10)
-        GBN_CASE(float, 11)
-        GBN_CASE(float, 12)
         default:
             return GBN_ERR_Q;
     }

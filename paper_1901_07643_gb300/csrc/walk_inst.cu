@@ -5,10 +5,10 @@
 #error "walk_inst.cu needs -DGBN_T=... -DGBN_Q=... -DGBN_COV=..."
 #endif
 
-#include "walk2.cuh"
+#include "walk3.cuh"
 
 #define GBN_XNAME(T, Q, C) GBN_WALK_INST_NAME(T, Q, C)
 int GBN_XNAME(GBN_T, GBN_Q, GBN_COV)(const gbn::WalkArgs<GBN_T>& a, int64_t n_cta,
                                       cudaStream_t s) {
-    return gbn::launch_walk_q<GBN_T, GBN_Q, (GBN_COV != 0), gbn::kConsumerSlots>(a, n_cta, s);
+    return gbn::launch_walk_q<GBN_T, GBN_Q, (GBN_COV != 0)>(a, n_cta, s);
 }

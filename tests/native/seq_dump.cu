@@ -2,13 +2,13 @@
 // CPU test can compare it with the oracle's GreedySwaps.  Host code only.
 #include <cstdio>
 
-#include "../../paper_1901_07643_gb300/csrc/walk2.cuh"
+#include "../../paper_1901_07643_gb300/csrc/walk3.cuh"
 
 template <int Q>
 void dump() {
     constexpr auto tab = gbn::make_step_tab<Q>();
     for (int t = 0; t < gbn::StepTab<Q>::N; ++t)
-        std::printf("%d %u %u\n", Q, (tab.e[t] & 15u) + 1u, tab.e[t] >> 4);
+        std::printf("%d %u %u\n", Q, (unsigned)tab.row[t] + 1u, (unsigned)tab.pre[t]);
 }
 
 int main() {

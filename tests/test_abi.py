@@ -49,13 +49,13 @@ def test_workspace_size_and_plan(lib):
     assert _ws(1000, 20, precision=1) > _ws(1000, 20, precision=0)
     for m in range(2, 31):
         q = binding.auto_q(m, 0)
-        assert 2 <= q <= min(12, m)
+        assert 2 <= q <= min(9, m)
         assert 2 <= binding.auto_q(m, 1) <= min(8, m)
 
 
 @pytest.mark.parametrize("n,m,kw,code", [
     (200, 1, {}, -1), (200, 31, {}, -1), (10, 10, {}, -2), (3, 3, {}, -2),
-    (200, 10, {"precision": 2}, -8), (200, 14, {"q": 13}, -7), (200, 10, {"q": 1}, -7),
+    (200, 10, {"precision": 2}, -8), (200, 14, {"q": 10}, -7), (200, 10, {"q": 1}, -7),
     (200, 4, {"q": 5}, -7), (200, 20, {"q": 9, "precision": 1}, -7),
 ])
 def test_argument_errors(lib, n, m, kw, code):
