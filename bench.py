@@ -33,7 +33,8 @@ if ROOT not in sys.path:
 METRIC = "family scores/sec (all m*2^(m-1)) at m=26, FP32 vs plain FP64, on 1 GB300"
 UNIT = "family scores/s"
 FALLBACK_HBM_GBS = 6800.0
-WALK_SOURCES = ["paper_1901_07643_gb300/csrc/walk.cuh", "paper_1901_07643_gb300/csrc/walk_inst.cu",
+WALK_SOURCES = ["paper_1901_07643_gb300/csrc/walk3.cuh", "paper_1901_07643_gb300/csrc/walk_inst.cu",
+                "paper_1901_07643_gb300/csrc/walk_dispatch.cu",
                 "paper_1901_07643_gb300/csrc/gbn_internal.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk_traffic.json")
 LAUNCHES_PER_STEP = 7  # colsum, gram x2, cholesky x2, roots, walk
@@ -273,7 +274,7 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def make(precision):
-        q = args.q if (args.q and (precision == 0 or args.q <= 7)) else 0
+        q = args.q if (args.q and (precision == 0 or args.q <= 8)) else 0
         out = torch.empty(fam, dtype=torch.float64 if precision else torch.float32, device=dev)
         ws = torch.empty(binding.workspace_size(w.n, w.m, precision, q), dtype=torch.uint8,
                          device=dev)

@@ -19,7 +19,7 @@
  * re-triangularised by one Givens rotation (the GRC operator of Sec. 1.3);
  * every R on the walk yields the RSS of the families whose parents are a
  * prefix of its column ordering (Sec. 2).  The sequence is split into
- * independent sub-walks as in Sec. 7 (Algorithm 2, corrected reading), one
+ * independent sub-walks as in Sec. 6 (Algorithm 2, corrected reading), one
  * per GPU lane.
  *
  * Conventions for every entry point:
@@ -88,7 +88,7 @@ int givensbn_workspace_size(int64_t n, int32_t m, const givensbn_opts* opts, siz
 
 /*
  * Scores of every family of the n x m data X (the problem of Sec. 1;
- * method of Sec. 1.3, Sec. 3 and Sec. 7).
+ * method of Sec. 1.3, Sec. 3 and Sec. 6).
  *   X          device, n x m FP64 row-major, read only
  *   out_scores device, m * 2^(m-1) elements: float (precision 0) or double
  *              (precision 1), or uint32 counters if opts->debug_coverage;

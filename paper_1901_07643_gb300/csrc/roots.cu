@@ -1,4 +1,4 @@
-// Roots of the sub-walks: the parallel split of Sec. 7 (Algorithm 2).
+// Roots of the sub-walks: the parallel split of Sec. 6 (Algorithm 2).
 //
 // A sub-walk is fixed by its front set F, a subset of the k fixed variables:
 // its ordering is [F, L, B] with L the Q free variables and B the fixed

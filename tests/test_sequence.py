@@ -140,7 +140,7 @@ def test_literal_split_reading_misses_prefix_sets():
 
 
 def test_split_swap_counts():
-    """Sec. 7: each of the 2^k processors performs 2^(m-k) - (m-k) - 1 swaps."""
+    """Sec. 6: each of the 2^k processors performs 2^(m-k) - (m-k) - 1 swaps."""
     for m, k in [(8, 3), (10, 4)]:
         for p in range(1 << k):
             bits = [(p >> b) & 1 for b in range(k)]
