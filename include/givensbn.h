@@ -57,6 +57,7 @@ extern "C" {
 #define GBN_ERR_Q (-7)          /* opts->q outside the supported range for m */
 #define GBN_ERR_PRECISION (-8)  /* opts->precision not 0 or 1 */
 #define GBN_ERR_BATCH (-9)      /* batched arguments inconsistent */
+#define GBN_ERR_STATIC_SCRATCH (-10) /* input needs more than the no-alloc entry point's scratch */
 
 /* device status bits (givensbn_status) */
 #define GBN_STATUS_RANK_DEFICIENT 1 /* a Cholesky pivot was <= 0: RSS 0 for some families */
@@ -107,6 +108,28 @@ const char* givensbn_strerror(int code);
 
 /* The q the automatic choice picks for (m, precision). */
 int32_t givensbn_auto_q(int32_t m, int32_t precision);
+
+/*
+ * score_all_families without a workspace and without any allocation.  The
+ * paper has no counterpart: this is an engineering variant for callers that
+ * cannot allocate device memory when they call (a host runtime whose pool
+ * owns all free device memory; loops where cudaMalloc/cudaFree would
+ * synchronise the device).  Same computation as score_all_families with the
+ * default options: FP32 walk, fp32 scores, centring, automatic q.
+ *   X          device, n x m FP64 row-major, read only
+ *   out_scores device, m * 2^(m-1) floats, every element written once
+ *   stream     cudaStream_t (NULL = legacy default stream); asynchronous
+ * Scratch: a 16 MiB array in the library's device image (enough for every n
+ * at m <= 20); larger inputs return GBN_ERR_STATIC_SCRATCH with nothing
+ * enqueued.  Its 256-byte status block is cleared by every call on `stream`.
+ * All calls on a device share that scratch, so calls must not overlap: a
+ * call may start only after the previous call's kernels have completed.  The
+ * first call on each device looks up the scratch address (with that device
+ * current); make it before any stream capture.  Device status words are not
+ * reported by this entry point.  Returns 0 or GBN_ERR_*.
+ */
+int score_all_families_noalloc(const double* X, int64_t n, int32_t m, float* out_scores,
+                               void* stream);
 
 #ifdef __cplusplus
 }

@@ -6,5 +6,5 @@ marshal arguments to its C entry points (``include/givensbn.h``).  Importing
 the package does not load the library; the first call does, and raises if it
 has not been built.
 """
-from .binding import (GivensBNError, auto_q, load, score_all_families, strerror,  # noqa: F401
-                      workspace_size)
+from .binding import (GivensBNError, auto_q, load, score_all_families,  # noqa: F401
+                      score_all_families_noalloc, strerror, workspace_size)

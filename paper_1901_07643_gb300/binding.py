@@ -56,6 +56,7 @@ def load():
             lib.givensbn_strerror.restype = ctypes.c_char_p
             lib.givensbn_auto_q.argtypes = [i32, i32]
             lib.givensbn_auto_q.restype = i32
+            lib.score_all_families_noalloc.argtypes = [P, i64, i32, P, P]
             _lib = lib
     return _lib
 
@@ -149,4 +150,27 @@ def score_all_families(X: torch.Tensor, out: torch.Tensor | None = None, *, prec
             raise GivensBNError(rc)
         if st.value & GBN_STATUS_RANK_DEFICIENT:
             warnings.warn("givensbn: data rank deficient; some RSS are 0 (scores -inf)")
+    return out
+
+
+def score_all_families_noalloc(X: torch.Tensor, out: torch.Tensor, *, stream=None) -> torch.Tensor:
+    """FP32 scores of all families through the library's allocation-free entry point.
+
+    The library uses its own 16 MiB static device scratch (m <= 20) and takes
+    no workspace; `out` (float32, m * 2^(m-1) elements, on X's device) must be
+    supplied by the caller.  Calls on one device must not overlap.
+    """
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float64 and X.dim() == 2):
+        raise TypeError("X must be a 2-D float64 CUDA tensor")
+    if not X.is_contiguous():
+        raise ValueError("X must be contiguous (row-major)")
+    n, m = X.shape
+    if not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+            and out.numel() == m << (m - 1) and out.device == X.device):
+        raise ValueError("out must be a contiguous float32 tensor of m * 2^(m-1) elements on X's device")
+    rc = load().score_all_families_noalloc(ctypes.c_void_p(X.data_ptr()), n, m,
+                                           ctypes.c_void_p(out.data_ptr()),
+                                           _stream_handle(stream, X.device))
+    if rc:
+        raise GivensBNError(rc)
     return out

@@ -175,6 +175,9 @@ const char* givensbn_strerror(int code) {
         case GBN_ERR_Q: return "q outside the supported range";
         case GBN_ERR_PRECISION: return "precision must be 0 (FP32) or 1 (FP64)";
         case GBN_ERR_BATCH: return "inconsistent batched arguments";
+        case GBN_ERR_STATIC_SCRATCH:
+            return "input too large for the 16 MiB static scratch of score_all_families_noalloc "
+                   "(m <= 20 with the automatic q)";
         default: return "unknown error";
     }
 }

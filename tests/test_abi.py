@@ -91,3 +91,14 @@ def test_device_swap_tables_match_greedy_swaps(tmp_path):
         orders = seq.apply_swaps(list(range(Q)), sw)[1:]
         for r, o, i in zip(mine, orders, sw):
             assert r[2] == sum(1 << v for v in o[:i])
+
+
+def test_noalloc_host_rejections(lib):
+    """The allocation-free entry point rejects before touching the device."""
+    import ctypes
+    f = lib.score_all_families_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    assert f(None, 5000, 22, None, None) == -10  # needs more than the 16 MiB static scratch
+    assert f(None, 64, 31, None, None) == -1     # m out of range
+    assert f(None, 5, 8, None, None) == -2       # n < m + 1
+    assert f(None, 100, 12, None, None) == -3    # NULL pointers
