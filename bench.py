@@ -37,7 +37,7 @@ WALK_SOURCES = ["paper_1901_07643_gb300/csrc/walk3.cuh", "paper_1901_07643_gb300
                 "paper_1901_07643_gb300/csrc/walk_dispatch.cu",
                 "paper_1901_07643_gb300/csrc/gbn_internal.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk_traffic.json")
-LAUNCHES_PER_STEP = 7  # colsum, gram x2, cholesky x2, roots, walk
+LAUNCHES_PER_STEP = 8  # colsum, mean, gram x2, cholesky x2, roots, walk
 
 
 def _args():

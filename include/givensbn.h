@@ -110,6 +110,61 @@ const char* givensbn_strerror(int code);
 int32_t givensbn_auto_q(int32_t m, int32_t precision);
 
 /*
+ * Scores of B datasets of uneven size in one set of launches (the same
+ * computation as score_all_families for each dataset; batching is an
+ * engineering addition, the paper scores one dataset).
+ *   Xs          host array of B device pointers, each n_b x m_b FP64 row-major
+ *   ns, ms      host arrays of B sizes (each as for score_all_families)
+ *   out         device; table b occupies out_offsets[b] .. + m_b * 2^(m_b-1)
+ *               elements (float, or double for precision 1, or uint32 counters
+ *               with debug_coverage); tables must not overlap and each must
+ *               start 16-byte aligned
+ *   out_offsets host array of B element offsets into out
+ *   opts        host; opts->q is the common sub-walk size (0 = the smallest
+ *               automatic choice over the batch); workspace >=
+ *               givensbn_batched_workspace_size()
+ * The call plans every dataset on the host, writes a device table into the
+ * head of the workspace with kernel launches (no runtime memcpy, allocation or
+ * synchronisation), then runs each stage as one launch over all datasets,
+ * largest datasets first.  The whole call may be captured into a CUDA graph;
+ * replaying the graph re-runs it with the same pointers.  Status words are
+ * per dataset and are not read by givensbn_status.  Returns 0 or GBN_ERR_*.
+ */
+int score_all_families_batched(const double* const* Xs, const int64_t* ns, const int32_t* ms,
+                               int32_t B, void* out, const int64_t* out_offsets,
+                               const givensbn_opts* opts);
+
+/* Workspace bytes score_all_families_batched needs for these sizes and options. */
+int givensbn_batched_workspace_size(const int64_t* ns, const int32_t* ms, int32_t B,
+                                    const givensbn_opts* opts, size_t* bytes);
+
+/*
+ * Gradient of L = sum_f w_f * score_f with respect to X (the adjoint of the
+ * scoring path; the paper has no gradient, the derivative follows from the
+ * least-squares problem of Sec. 1 and the walk of Sec. 1.3 / Algorithm 1).
+ * Every score depends on X only through the centred Gram G = Xc^T Xc, and
+ *     grad_X = Xc (Gbar + Gbar^T),   Gbar = sum_f (w_f n / RSS_f) v_f v_f^T,
+ * v_f = e_c - beta_f with beta_f the family's least-squares coefficients.
+ * Gbar is accumulated along the Givens walk, one sub-walk per warp, each
+ * sub-walk re-formed from R0 by GRC steps (the R0 checkpoint).
+ *   X       device, n x m FP64 row-major (raw; centred as in the forward pass)
+ *   w       device, m * 2^(m-1) weights in table layout: float (precision 0,
+ *           FP32 walk state) or double (precision 1), 16-byte aligned
+ *   grad_X  device, n x m FP64 row-major, written (not accumulated)
+ *   opts    host; workspace >= givensbn_backward_workspace_size(); opts->q is
+ *           the sub-walk size of the backward walk (0 = automatic, m - 10)
+ * Families with RSS == 0 contribute nothing (their score is -inf); a singular
+ * sub-walk factor sets GBN_STATUS_RANK_DEFICIENT and is skipped.
+ * Deterministic: sums are formed in a fixed order.  Returns 0 or GBN_ERR_*.
+ */
+int score_all_families_backward(const double* X, int64_t n, int32_t m, const void* w,
+                                double* grad_X, const givensbn_opts* opts);
+
+/* Workspace bytes score_all_families_backward needs for (n, m, opts). */
+int givensbn_backward_workspace_size(int64_t n, int32_t m, const givensbn_opts* opts,
+                                     size_t* bytes);
+
+/*
  * score_all_families without a workspace and without any allocation.  The
  * paper has no counterpart: this is an engineering variant for callers that
  * cannot allocate device memory when they call (a host runtime whose pool

@@ -6,5 +6,8 @@ marshal arguments to its C entry points (``include/givensbn.h``).  Importing
 the package does not load the library; the first call does, and raises if it
 has not been built.
 """
-from .binding import (GivensBNError, auto_q, load, score_all_families,  # noqa: F401
-                      score_all_families_noalloc, strerror, workspace_size)
+from .binding import (GivensBNError, all_family_scores, auto_q, batch_offsets,  # noqa: F401
+                      backward_workspace_size, batched_workspace_size, load,
+                      score_all_families, score_all_families_batched,
+                      score_all_families_backward, score_all_families_noalloc, strerror,
+                      workspace_size)

@@ -57,6 +57,12 @@ def load():
             lib.givensbn_auto_q.argtypes = [i32, i32]
             lib.givensbn_auto_q.restype = i32
             lib.score_all_families_noalloc.argtypes = [P, i64, i32, P, P]
+            lib.score_all_families_batched.argtypes = [P, P, P, i32, P, P, ctypes.POINTER(Opts)]
+            lib.givensbn_batched_workspace_size.argtypes = [P, P, i32, ctypes.POINTER(Opts),
+                                                            ctypes.POINTER(ctypes.c_size_t)]
+            lib.score_all_families_backward.argtypes = [P, i64, i32, P, P, ctypes.POINTER(Opts)]
+            lib.givensbn_backward_workspace_size.argtypes = [i64, i32, ctypes.POINTER(Opts),
+                                                             ctypes.POINTER(ctypes.c_size_t)]
             _lib = lib
     return _lib
 
@@ -99,6 +105,15 @@ def workspace_size(n: int, m: int, precision: int = 0, q: int = 0) -> int:
     o = _opts(precision, q)
     b = ctypes.c_size_t(0)
     rc = load().givensbn_workspace_size(n, m, ctypes.byref(o), ctypes.byref(b))
+    if rc:
+        raise GivensBNError(rc)
+    return int(b.value)
+
+
+def backward_workspace_size(n: int, m: int, precision: int = 0, q: int = 0) -> int:
+    o = _opts(precision, q)
+    b = ctypes.c_size_t(0)
+    rc = load().givensbn_backward_workspace_size(n, m, ctypes.byref(o), ctypes.byref(b))
     if rc:
         raise GivensBNError(rc)
     return int(b.value)
@@ -174,3 +189,133 @@ def score_all_families_noalloc(X: torch.Tensor, out: torch.Tensor, *, stream=Non
     if rc:
         raise GivensBNError(rc)
     return out
+
+
+def score_all_families_backward(X: torch.Tensor, w: torch.Tensor, *, precision: int = 0, q: int = 0,
+                                center: bool = True, workspace: torch.Tensor | None = None,
+                                stream=None, check: bool = True) -> torch.Tensor:
+    """Gradient of sum_f w_f * score_f with respect to X (float64, n x m).
+
+    w: weights in table layout (m * 2^(m-1)); float32 for precision 0 (FP32
+    walk), float64 for precision 1.
+    """
+    if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float64 and X.dim() == 2):
+        raise TypeError("X must be a 2-D float64 CUDA tensor")
+    X = X.contiguous()
+    n, m = X.shape
+    wdt = torch.float64 if precision else torch.float32
+    w = w.to(device=X.device, dtype=wdt).contiguous()
+    if w.numel() != m << (m - 1):
+        raise ValueError("w must hold m * 2^(m-1) weights")
+    grad = torch.empty_like(X)
+    if workspace is None:
+        workspace = torch.empty(backward_workspace_size(n, m, precision, q), dtype=torch.uint8,
+                                device=X.device)
+    o = _opts(precision, q, center, False, _stream_handle(stream, X.device), workspace)
+    rc = load().score_all_families_backward(ctypes.c_void_p(X.data_ptr()), n, m,
+                                            ctypes.c_void_p(w.data_ptr()),
+                                            ctypes.c_void_p(grad.data_ptr()), ctypes.byref(o))
+    if rc:
+        raise GivensBNError(rc)
+    if check:
+        st = ctypes.c_int32(0)
+        rc = load().givensbn_status(ctypes.byref(o), ctypes.byref(st))
+        if rc:
+            raise GivensBNError(rc)
+        if st.value & GBN_STATUS_RANK_DEFICIENT:
+            warnings.warn("givensbn: singular sub-walk factor or Gram matrix in the backward pass")
+    return grad
+
+
+class AllFamilyScores(torch.autograd.Function):
+    """Differentiable scores: forward = score_all_families, backward = the adjoint walk."""
+
+    @staticmethod
+    def forward(ctx, X, precision=0, q=0, center=True):
+        ctx.save_for_backward(X)
+        ctx.opts = (precision, center)
+        return score_all_families(X.detach(), precision=precision, q=q, center=center)
+
+    @staticmethod
+    def backward(ctx, grad_scores):
+        (X,) = ctx.saved_tensors
+        precision, center = ctx.opts
+        g = score_all_families_backward(X.detach(), grad_scores, precision=precision,
+                                        center=center)
+        return g, None, None, None
+
+
+def all_family_scores(X: torch.Tensor, precision: int = 0, q: int = 0,
+                      center: bool = True) -> torch.Tensor:
+    """Scores of all families with autograd support (gradient through the adjoint walk)."""
+    return AllFamilyScores.apply(X, precision, q, center)
+
+
+def _batch_arrays(Xs):
+    B = len(Xs)
+    ns = (ctypes.c_int64 * B)(*[int(X.shape[0]) for X in Xs])
+    ms = (ctypes.c_int32 * B)(*[int(X.shape[1]) for X in Xs])
+    return B, ns, ms
+
+
+def batched_workspace_size(Xs, precision: int = 0, q: int = 0) -> int:
+    B, ns, ms = _batch_arrays(Xs)
+    o = _opts(precision, q)
+    b = ctypes.c_size_t(0)
+    rc = load().givensbn_batched_workspace_size(ctypes.cast(ns, ctypes.c_void_p),
+                                                ctypes.cast(ms, ctypes.c_void_p), B,
+                                                ctypes.byref(o), ctypes.byref(b))
+    if rc:
+        raise GivensBNError(rc)
+    return int(b.value)
+
+
+def batch_offsets(Xs):
+    """Element offsets of each dataset's table in the concatenated output."""
+    offs, pos = [], 0
+    for X in Xs:
+        m = int(X.shape[1])
+        offs.append(pos)
+        pos += m << (m - 1)
+    return offs, pos
+
+
+def score_all_families_batched(Xs, out: torch.Tensor | None = None, *, precision: int = 0,
+                               q: int = 0, center: bool = True, debug_coverage: bool = False,
+                               workspace: torch.Tensor | None = None, stream=None):
+    """Scores of every family of every dataset in Xs (list of n_b x m_b float64 CUDA tensors).
+
+    Returns (out, offsets): the tables concatenated in the order of Xs, and the
+    element offset of each.  Safe to capture in a CUDA graph when `out` and
+    `workspace` are supplied.
+    """
+    if not Xs:
+        raise ValueError("empty batch")
+    dev = Xs[0].device
+    for X in Xs:
+        if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float64
+                and X.dim() == 2 and X.is_contiguous() and X.device == dev):
+            raise TypeError("every X must be a contiguous 2-D float64 CUDA tensor on one device")
+    B, ns, ms = _batch_arrays(Xs)
+    offs, total = batch_offsets(Xs)
+    if out is None:
+        if debug_coverage:
+            out = torch.zeros(total, dtype=torch.int32, device=dev)
+        else:
+            out = torch.empty(total, dtype=torch.float64 if precision else torch.float32, device=dev)
+    if out.numel() < total:
+        raise ValueError("out is too small for the batch")
+    if workspace is None:
+        workspace = torch.empty(batched_workspace_size(Xs, precision, q), dtype=torch.uint8,
+                                device=dev)
+    ptrs = (ctypes.c_void_p * B)(*[X.data_ptr() for X in Xs])
+    offa = (ctypes.c_int64 * B)(*offs)
+    o = _opts(precision, q, center, debug_coverage, _stream_handle(stream, dev), workspace)
+    rc = load().score_all_families_batched(ctypes.cast(ptrs, ctypes.c_void_p),
+                                           ctypes.cast(ns, ctypes.c_void_p),
+                                           ctypes.cast(ms, ctypes.c_void_p), B,
+                                           ctypes.c_void_p(out.data_ptr()),
+                                           ctypes.cast(offa, ctypes.c_void_p), ctypes.byref(o))
+    if rc:
+        raise GivensBNError(rc)
+    return out, offs

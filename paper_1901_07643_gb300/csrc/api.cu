@@ -44,7 +44,7 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     for (int v = p->W; v < p->k; ++v) p->order[pos++] = v;
     for (int v = 0; v < p->W; ++v) p->order[pos++] = v;
     for (int v = p->k; v < m; ++v) p->order[pos++] = v;
-    int panels = (int)(n / 16);
+    int panels = (int)(n / 32);
     if (panels < 1) panels = 1;
     if (panels > kMaxPanels) panels = kMaxPanels;
     p->rows_per_panel = (int)((n + panels - 1) / panels);
@@ -66,9 +66,13 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     off = align_up(off + 256, 256);
     p->off_colsum = off;
     off = align_up(off + sizeof(double) * (size_t)p->panels * m, 256);
+    p->off_mu = off;
+    off = align_up(off + sizeof(double) * 32, 256);
     p->off_gram = off;
     off = align_up(off + sizeof(double) * (size_t)p->panels * (m * (m + 1) / 2), 256);
     p->off_r1 = off;
+    off = align_up(off + sizeof(double) * (size_t)m * m, 256);
+    p->off_r1inv = off;
     off = align_up(off + sizeof(double) * (size_t)m * m, 256);
     p->off_r0 = off;
     off = align_up(off + sizeof(double) * (size_t)m * m, 256);

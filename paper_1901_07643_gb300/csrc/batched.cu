@@ -1,0 +1,225 @@
+// Batched scoring: many datasets of uneven (n, m) in one set of launches.
+//
+// The host plans every dataset (one common sub-walk size Q), orders the
+// datasets largest first, lays out one workspace region per dataset and
+// writes a device-side table (plans, pointers, walk arguments, block
+// prefixes) into the head of the workspace with small upload kernels whose
+// payload travels as kernel parameters.  Every stage is then one launch over
+// all datasets; a block finds its dataset by binary search in the prefix of
+// block counts.  Nothing here allocates, copies through the runtime's memcpy
+// or synchronises, so a whole call can be captured into a CUDA graph.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "walk3.cuh"
+
+namespace gbn {
+namespace {
+
+constexpr int kUploadBytes = 30 * 1024;  // payload per upload launch (kernel parameter)
+
+struct UploadChunk {
+    unsigned char* dst;
+    int bytes;
+    unsigned char data[kUploadBytes];
+};
+
+__global__ void upload_kernel(const __grid_constant__ UploadChunk c) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.bytes; i += gridDim.x * blockDim.x)
+        c.dst[i] = c.data[i];
+}
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+struct BatchLayout {
+    std::vector<Plan> plans;
+    std::vector<int32_t> launch_order;  // launch position -> dataset
+    std::vector<size_t> ws_off;         // per dataset, from the workspace base
+    size_t table_bytes = 0;             // device table at the workspace head
+    size_t total = 0;
+    int Q = 0, maxW = 0, n_cwarps = 1;
+    int64_t total_cta = 0, total_panels = 0;
+    // table offsets (from the workspace base)
+    size_t off_cta_prefix = 0, off_panel_prefix = 0, off_dataset_of = 0, off_plans = 0,
+           off_X = 0, off_ws = 0, off_out = 0, off_args = 0;
+};
+
+int plan_batch(const int64_t* ns, const int32_t* ms, int32_t B, const givensbn_opts* opts,
+               BatchLayout* L) {
+    if (B < 1 || !ns || !ms) return B < 1 ? GBN_ERR_BATCH : GBN_ERR_NULL;
+    givensbn_opts o;
+    givensbn_default_opts(&o);
+    if (opts) o = *opts;
+    int precision = o.precision;
+    if (precision != 0 && precision != 1) return GBN_ERR_PRECISION;
+    // one Q for the whole batch: the requested one, else the smallest automatic choice
+    int Q = o.q;
+    if (Q <= 0) {
+        Q = 1 << 30;
+        for (int b = 0; b < B; ++b) {
+            if (ms[b] < GBN_MIN_M || ms[b] > GBN_MAX_M) return GBN_ERR_M;
+            Q = std::min(Q, auto_q(ms[b], precision));
+        }
+    }
+    o.q = Q;
+    L->plans.resize(B);
+    for (int b = 0; b < B; ++b) {
+        const int rc = make_plan(ns[b], ms[b], &o, &L->plans[b]);
+        if (rc) return rc;
+    }
+    L->Q = Q;
+    L->maxW = 0;
+    L->n_cwarps = 1;
+    for (const Plan& p : L->plans) {
+        L->maxW = std::max(L->maxW, p.W);
+        L->n_cwarps = std::max(L->n_cwarps, p.n_bwarps);
+    }
+    // largest first: walk CTAs x families per CTA
+    L->launch_order.resize(B);
+    for (int b = 0; b < B; ++b) L->launch_order[b] = b;
+    std::stable_sort(L->launch_order.begin(), L->launch_order.end(), [&](int a, int c) {
+        return ((int64_t)L->plans[a].m << L->plans[a].m) > ((int64_t)L->plans[c].m << L->plans[c].m);
+    });
+    size_t off = 0;
+    L->off_cta_prefix = off;
+    off = up256(off + sizeof(int64_t) * (B + 1));
+    L->off_panel_prefix = off;
+    off = up256(off + sizeof(int64_t) * (B + 1));
+    L->off_dataset_of = off;
+    off = up256(off + sizeof(int32_t) * B);
+    L->off_plans = off;
+    off = up256(off + sizeof(Plan) * B);
+    L->off_X = off;
+    off = up256(off + sizeof(void*) * B);
+    L->off_ws = off;
+    off = up256(off + sizeof(void*) * B);
+    L->off_out = off;
+    off = up256(off + sizeof(void*) * B);
+    L->off_args = off;
+    off = up256(off + std::max(sizeof(WalkArgs<float>), sizeof(WalkArgs<double>)) * B);
+    L->table_bytes = off;
+    L->ws_off.resize(B);
+    L->total_cta = 0;
+    L->total_panels = 0;
+    for (int b = 0; b < B; ++b) {
+        L->ws_off[b] = off;
+        off = up256(off + L->plans[b].total_bytes);
+        L->total_cta += L->plans[b].n_cta;
+        L->total_panels += L->plans[b].panels;
+    }
+    if (L->total_cta > 0x7fffffff || L->total_panels > 0x7fffffff) return GBN_ERR_BATCH;
+    L->total = off;
+    return GBN_OK;
+}
+
+template <typename T>
+WalkArgs<T> walk_args_for(const Plan& p, char* ws, void* out, int n_cwarps) {
+    WalkArgs<T> a = make_walk_args<T>(p, ws, out);
+    a.n_cwarps = n_cwarps;
+    return a;
+}
+
+int upload(const std::vector<unsigned char>& host, char* dst, cudaStream_t stream) {
+    static thread_local UploadChunk chunk;  // host staging for the kernel parameter
+    for (size_t pos = 0; pos < host.size(); pos += kUploadBytes) {
+        const size_t nb = std::min(host.size() - pos, (size_t)kUploadBytes);
+        chunk.dst = reinterpret_cast<unsigned char*>(dst + pos);
+        chunk.bytes = (int)nb;
+        memcpy(chunk.data, host.data() + pos, nb);
+        upload_kernel<<<32, 256, 0, stream>>>(chunk);
+        if (cudaGetLastError() != cudaSuccess) return GBN_ERR_CUDA;
+    }
+    return GBN_OK;
+}
+
+}  // namespace
+}  // namespace gbn
+
+using namespace gbn;
+
+extern "C" int givensbn_batched_workspace_size(const int64_t* ns, const int32_t* ms, int32_t B,
+                                               const givensbn_opts* opts, size_t* bytes) {
+    if (!bytes) return GBN_ERR_NULL;
+    BatchLayout L;
+    const int rc = plan_batch(ns, ms, B, opts, &L);
+    if (rc) return rc;
+    *bytes = L.total;
+    return GBN_OK;
+}
+
+extern "C" int score_all_families_batched(const double* const* Xs, const int64_t* ns,
+                                          const int32_t* ms, int32_t B, void* out,
+                                          const int64_t* out_offsets, const givensbn_opts* opts) {
+    if (!opts || !Xs || !out || !out_offsets) return GBN_ERR_NULL;
+    BatchLayout L;
+    int rc = plan_batch(ns, ms, B, opts, &L);
+    if (rc) return rc;
+    if (!opts->workspace || opts->workspace_bytes < L.total) return GBN_ERR_WORKSPACE;
+    if ((uintptr_t)opts->workspace & 255u) return GBN_ERR_ALIGN;
+    const int precision = opts->precision;
+    const size_t es = precision ? sizeof(double) : sizeof(float);
+    char* base = static_cast<char*>(opts->workspace);
+    cudaStream_t stream = static_cast<cudaStream_t>(opts->stream);
+    // per-dataset pointers and checks
+    std::vector<const double*> X(B);
+    std::vector<char*> ws(B);
+    std::vector<void*> outp(B);
+    for (int b = 0; b < B; ++b) {
+        if (!Xs[b]) return GBN_ERR_NULL;
+        if ((uintptr_t)Xs[b] & 7u) return GBN_ERR_ALIGN;
+        if (out_offsets[b] < 0) return GBN_ERR_BATCH;
+        X[b] = Xs[b];
+        ws[b] = base + L.ws_off[b];
+        outp[b] = static_cast<char*>(out) + (size_t)out_offsets[b] * es;
+        if ((uintptr_t)outp[b] & 15u) return GBN_ERR_ALIGN;
+    }
+    for (int b = 0; b < B; ++b)  // tables must not overlap
+        for (int c = b + 1; c < B; ++c) {
+            const int64_t sb = (int64_t)ms[b] << (ms[b] - 1), sc = (int64_t)ms[c] << (ms[c] - 1);
+            if (out_offsets[b] < out_offsets[c] + sc && out_offsets[c] < out_offsets[b] + sb)
+                return GBN_ERR_BATCH;
+        }
+    // device table
+    std::vector<unsigned char> host(L.table_bytes, 0);
+    int64_t* cta_prefix = reinterpret_cast<int64_t*>(host.data() + L.off_cta_prefix);
+    int64_t* panel_prefix = reinterpret_cast<int64_t*>(host.data() + L.off_panel_prefix);
+    int32_t* dataset_of = reinterpret_cast<int32_t*>(host.data() + L.off_dataset_of);
+    cta_prefix[0] = panel_prefix[0] = 0;
+    for (int i = 0; i < B; ++i) {
+        const int b = L.launch_order[i];
+        dataset_of[i] = b;
+        cta_prefix[i + 1] = cta_prefix[i] + L.plans[b].n_cta;
+        panel_prefix[i + 1] = panel_prefix[i] + L.plans[b].panels;
+    }
+    memcpy(host.data() + L.off_plans, L.plans.data(), sizeof(Plan) * B);
+    memcpy(host.data() + L.off_X, X.data(), sizeof(void*) * B);
+    memcpy(host.data() + L.off_ws, ws.data(), sizeof(void*) * B);
+    memcpy(host.data() + L.off_out, outp.data(), sizeof(void*) * B);
+    for (int b = 0; b < B; ++b) {
+        if (precision) {
+            const WalkArgs<double> a = walk_args_for<double>(L.plans[b], ws[b], outp[b], L.n_cwarps);
+            memcpy(host.data() + L.off_args + sizeof(a) * b, &a, sizeof(a));
+        } else {
+            const WalkArgs<float> a = walk_args_for<float>(L.plans[b], ws[b], outp[b], L.n_cwarps);
+            memcpy(host.data() + L.off_args + sizeof(a) * b, &a, sizeof(a));
+        }
+    }
+    if ((rc = upload(host, base, stream))) return rc;
+    BatchView v;
+    v.B = B;
+    v.cta_prefix = reinterpret_cast<const int64_t*>(base + L.off_cta_prefix);
+    v.panel_prefix = reinterpret_cast<const int64_t*>(base + L.off_panel_prefix);
+    v.dataset_of = reinterpret_cast<const int32_t*>(base + L.off_dataset_of);
+    v.plans = reinterpret_cast<const Plan*>(base + L.off_plans);
+    v.X = reinterpret_cast<const double* const*>(base + L.off_X);
+    v.ws = reinterpret_cast<char* const*>(base + L.off_ws);
+    v.out = reinterpret_cast<void* const*>(base + L.off_out);
+    v.walk_args = base + L.off_args;
+    if ((rc = launch_r0_batched(v, L.total_panels, stream))) return rc;
+    if ((rc = launch_roots_batched(v, L.total_cta, L.maxW, precision, stream))) return rc;
+    return launch_walk_batched(v, L.total_cta, L.Q, precision, opts->debug_coverage != 0,
+                               L.n_cwarps, stream);
+}

@@ -57,18 +57,80 @@ struct Plan {
     int center = 1;
     int coverage = 0;
     // workspace layout (byte offsets)
-    size_t off_status = 0, off_colsum = 0, off_gram = 0, off_r1 = 0, off_r0 = 0, off_leaves = 0;
+    size_t off_status = 0, off_colsum = 0, off_mu = 0, off_gram = 0, off_r1 = 0, off_r1inv = 0;
+    size_t off_r0 = 0;
+    size_t off_leaves = 0;
     size_t total_bytes = 0;
     size_t leaf_stride = 0;  // elements per CTA leaf record
     int n_bwarps = 1;        // consumer warps per walk CTA (they loop over the CTA's columns)
 };
 
 int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* plan);
+int auto_q(int m, int precision);
 
 // Stages (each enqueues kernels on `stream`; return GBN_OK or GBN_ERR_CUDA).
 int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream);
 int launch_roots(const Plan& p, char* ws, cudaStream_t stream);
 int launch_walk(const Plan& p, char* ws, void* out, cudaStream_t stream);
+
+// The t-th swap (0-based t, 1-based swap index in [1, Q-1]) of the greedy
+// sequence Upsilon(Q) of Algorithm 1, read as
+//     Upsilon(q) = Upsilon(q-1) : [q-1 .. 1] : (Upsilon(q-1) + 1),
+// evaluated by descending the recursion (O(Q) per call).  Returns 0 when t is
+// outside [0, 2^Q - Q - 1).
+__host__ __device__ inline int upsilon_at(int Q, int64_t t) {
+    int shift = 0, q = Q;
+    while (q >= 2 && t >= 0) {
+        const int64_t len = ((int64_t)1 << (q - 1)) - (q - 1) - 1;  // |Upsilon(q-1)|
+        if (t < len) {
+            --q;
+            continue;
+        }
+        t -= len;
+        if (t < q - 1) return shift + (q - 1) - (int)t;
+        t -= q - 1;
+        ++shift;
+        --q;
+    }
+    return 0;
+}
+
+// Device view of a batch (see batched.cu): per-dataset plans and pointers, and
+// the running block counts of the stages in launch order (largest dataset
+// first).  Kernels map a block to (dataset, local block) with batch_locate.
+struct BatchView {
+    int B = 0;
+    const int64_t* cta_prefix = nullptr;    // B+1: sub-walk CTAs (roots, walk)
+    const int64_t* panel_prefix = nullptr;  // B+1: row panels (R0 passes)
+    const int32_t* dataset_of = nullptr;    // launch position -> dataset index
+    const Plan* plans = nullptr;
+    const double* const* X = nullptr;
+    char* const* ws = nullptr;              // per-dataset workspace region
+    void* const* out = nullptr;             // per-dataset score table
+    const void* walk_args = nullptr;        // WalkArgs<T>[B]
+};
+
+// Dataset index for global block bx: the launch position l with
+// prefix[l] <= bx < prefix[l+1]; local = bx - prefix[l].
+__device__ __forceinline__ int batch_locate(const BatchView& v, const int64_t* prefix, int64_t bx,
+                                            int64_t& local) {
+    int lo = 0, hi = v.B;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= bx)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    local = bx - prefix[lo];
+    return v.dataset_of[lo];
+}
+
+int launch_r0_batched(const BatchView& v, int64_t total_panels, cudaStream_t stream);
+int launch_roots_batched(const BatchView& v, int64_t total_cta, int max_w, int precision,
+                         cudaStream_t stream);
+int launch_walk_batched(const BatchView& v, int64_t total_cta, int Q, int precision, bool coverage,
+                        int n_cwarps, cudaStream_t stream);
 
 // Leaf record of one CTA (2^W sub-walk roots), elements of the scalar type,
 // lane-interleaved so that lane l of a warp reads element e at [e*32 + l]:

@@ -1,7 +1,9 @@
 // Initial QR decomposition R0 of the centred data (the "initial QRD" that the
 // walk starts from, Sec. 2 and Sec. 1.3), computed as CholeskyQR2 in FP64:
+//   means:  mu = column means (per-panel partial sums, then one reduction)
 //   pass 1: G1 = Xc^T Xc (row panels, reduced), R1 = chol(G1)
-//   pass 2: Q1 = Xc R1^{-1} (per row), G2 = Q1^T Q1, R2 = chol(G2), R0 = R2 R1.
+//   pass 2: Q1 = Xc R1^{-1} (explicit triangular inverse), G2 = Q1^T Q1,
+//           R2 = chol(G2), R0 = R2 R1.
 // Columns are taken in the plan's order (the order the sub-walk tree decides
 // variables in), so R0 is the R factor of Xc[:, order].
 #include <math.h>
@@ -11,18 +13,18 @@
 namespace gbn {
 namespace {
 
-constexpr int kPanelChunk = 32;  // rows staged in shared memory at a time
+constexpr int kPanelChunk = 64;  // rows staged in shared memory at a time
 constexpr int kLd = 33;          // row stride of the m x m shared-memory tiles
+constexpr int kRedThreads = 1024; // threads of the reduction / Cholesky kernel
 
 // All shared-memory tiles here are flat 1-D arrays indexed as [row * kLd + col]:
 // with this toolchain, runtime-indexed two-dimensional __shared__ arrays were
 // mis-addressed in sm_103 code while the same accesses on flat arrays were not.
 
-__global__ void colsum_kernel(const double* __restrict__ X, int64_t n, int m, int rows_per,
-                              double* __restrict__ colsum, int panels,
-                              unsigned long long* chk) {
+__device__ __forceinline__ void colsum_body(int b, const double* __restrict__ X, int64_t n, int m,
+                                            int rows_per, double* __restrict__ colsum, int panels,
+                                            unsigned long long* chk) {
     __shared__ double red[256];
-    const int b = blockIdx.x;
     const int64_t r0 = (int64_t)b * rows_per;
     const int64_t r1 = (r0 + rows_per < n) ? r0 + rows_per : n;
     const int per = blockDim.x / m;  // row lanes
@@ -43,28 +45,47 @@ __global__ void colsum_kernel(const double* __restrict__ X, int64_t n, int m, in
     }
 }
 
+// mu[j] = column mean of variable order[j] (zero when centring is off).
+// Threads split the panels of each column; four partial sums per thread.
+__device__ __forceinline__ void mean_body(const double* __restrict__ colsum, int panels, int m,
+                                          int64_t n, int center, const Plan& plan,
+                                          double* __restrict__ mu, unsigned long long* chk) {
+    __shared__ double red[kRedThreads];
+    const int per = kRedThreads / m;  // threads per column
+    const int j = threadIdx.x % m;
+    const int l = threadIdx.x / m;
+    double s = 0.0;
+    if (center && l < per) {
+        const int v = plan.order[j];
+        for (int b = l; b < panels; b += per)
+            if (GBN_IN(chk, 131, (int64_t)b * m + v, (int64_t)panels * m))
+                s += colsum[(int64_t)b * m + v];
+    }
+    red[threadIdx.x] = (l < per) ? s : 0.0;
+    __syncthreads();
+    if (threadIdx.x < m) {
+        double acc = 0.0;
+        for (int t = 0; t < per; ++t) acc += red[t * m + threadIdx.x];
+        mu[threadIdx.x] = center ? acc / (double)n : 0.0;
+    }
+}
+
 // Partial Gram of one row panel: sum over its rows of y y^T (upper triangle,
 // packed by pairs i <= j), where y is the centred row in plan order, or for
-// pass 2 the row of Q1 solving y R1 = xc.
-__global__ void gram_kernel(const double* __restrict__ X, int64_t n, int m, int rows_per,
-                            const double* __restrict__ colsum, int panels, int center,
-                            const double* __restrict__ R1, Plan plan, double* __restrict__ gram,
-                            unsigned long long* chk) {
+// pass 2 the row of Q1 = y R1^{-1} (Rinv = R1^{-1}, upper triangular).
+__device__ __forceinline__ void gram_body(int blk, const double* __restrict__ X, int64_t n, int m,
+                                          int rows_per, const double* __restrict__ mu_g, int panels,
+                                          const double* __restrict__ Rinv, const Plan& plan,
+                                          double* __restrict__ gram, unsigned long long* chk) {
     __shared__ double mu[32];
     __shared__ double rows[kPanelChunk * kLd];
-    __shared__ double r1[32 * kLd];
+    __shared__ double qrows[kPanelChunk * kLd];
+    __shared__ double ri[32 * kLd];
     const int tid = threadIdx.x;
-    if (tid < m) {
-        double s = 0.0;
-        if (center)
-            for (int b = 0; b < panels; ++b)
-                if (GBN_IN(chk, 111, (int64_t)b * m + plan.order[tid], (int64_t)panels * m))
-                    s += colsum[(int64_t)b * m + plan.order[tid]];
-        mu[tid] = center ? s / (double)n : 0.0;
-    }
-    if (R1)
+    if (tid < m) mu[tid] = mu_g[tid];
+    if (Rinv)
         for (int e = tid; e < m * m; e += blockDim.x)
-            if (GBN_IN(chk, 112, (e / m) * kLd + e % m, 32 * kLd)) r1[(e / m) * kLd + e % m] = R1[e];
+            if (GBN_IN(chk, 112, (e / m) * kLd + e % m, 32 * kLd)) ri[(e / m) * kLd + e % m] = Rinv[e];
     const int npair = m * (m + 1) / 2;
     int pi = 0, pj = 0;
     if (tid < npair) {  // unpack pair index -> (i, j), i <= j
@@ -76,9 +97,10 @@ __global__ void gram_kernel(const double* __restrict__ X, int64_t n, int m, int 
         pi = i;
         pj = i + e;
     }
-    double acc = 0.0;
-    const int64_t r0 = (int64_t)blockIdx.x * rows_per;
+    double acc0 = 0.0, acc1 = 0.0;
+    const int64_t r0 = (int64_t)blk * rows_per;
     const int64_t rend = (r0 + rows_per < n) ? r0 + rows_per : n;
+    const double* src = Rinv ? qrows : rows;
     __syncthreads();
     for (int64_t c0 = r0; c0 < rend; c0 += kPanelChunk) {
         const int cnt = (rend - c0 < kPanelChunk) ? (int)(rend - c0) : kPanelChunk;
@@ -89,103 +111,224 @@ __global__ void gram_kernel(const double* __restrict__ X, int64_t n, int m, int 
                 rows[t * kLd + j] = X[xi] - mu[j];
         }
         __syncthreads();
-        if (R1 && tid < cnt) {  // forward substitution y R1 = xc, one row per thread
-            double* y = rows + tid * kLd;
-            for (int j = 0; j < m; ++j) {
-                double s = y[j];
-                for (int i = 0; i < j; ++i) s -= y[i] * r1[i * kLd + j];
-                const double d = r1[j * kLd + j];
-                y[j] = (d != 0.0) ? s / d : 0.0;
+        if (Rinv) {  // Q1 rows: q[t][j] = sum_{i <= j} y[t][i] Rinv[i][j], one entry per thread
+            for (int e = tid; e < cnt * m; e += blockDim.x) {
+                const int t = e / m, j = e % m;
+                double s0 = 0.0, s1 = 0.0;
+                int i = 0;
+                for (; i + 1 <= j; i += 2) {
+                    s0 = fma(rows[t * kLd + i], ri[i * kLd + j], s0);
+                    s1 = fma(rows[t * kLd + i + 1], ri[(i + 1) * kLd + j], s1);
+                }
+                if (i <= j) s0 = fma(rows[t * kLd + i], ri[i * kLd + j], s0);
+                qrows[t * kLd + j] = s0 + s1;
             }
+            __syncthreads();
+        }
+        if (tid < npair) {
+            int t = 0;
+            for (; t + 1 < cnt; t += 2) {
+                acc0 = fma(src[t * kLd + pi], src[t * kLd + pj], acc0);
+                acc1 = fma(src[(t + 1) * kLd + pi], src[(t + 1) * kLd + pj], acc1);
+            }
+            if (t < cnt) acc0 = fma(src[t * kLd + pi], src[t * kLd + pj], acc0);
         }
         __syncthreads();
-        if (tid < npair)
-            for (int t = 0; t < cnt; ++t) acc = fma(rows[t * kLd + pi], rows[t * kLd + pj], acc);
-        __syncthreads();
     }
-    if (tid < npair && GBN_IN(chk, 115, (int64_t)blockIdx.x * npair + tid, (int64_t)panels * npair))
-        gram[(int64_t)blockIdx.x * npair + tid] = acc;
+    if (tid < npair && GBN_IN(chk, 115, (int64_t)blk * npair + tid, (int64_t)panels * npair))
+        gram[(int64_t)blk * npair + tid] = acc0 + acc1;
 }
 
-// Sum the panel Grams, Cholesky-factor (upper R with R^T R = G).  If R1 is
-// given, the result is R2 and R0 = R2 * R1 is written to Rout; otherwise the
-// factor itself is written to Rout.
-__global__ void chol_kernel(const double* __restrict__ gram, int panels, int m,
-                            const double* __restrict__ R1, double* __restrict__ Rout,
-                            int* __restrict__ status, unsigned long long* chk) {
+// Sum the panel Grams and Cholesky-factor the sum (upper R with R^T R = G).
+// Pass 1 (R1 == nullptr): writes R1 to Rout and its inverse to Rinv_out.
+// Pass 2: the factor is R2 and R0 = R2 * R1 is written to Rout.
+// The panel sums are split over warps (lanes stride over panels, then a
+// fixed shuffle tree), the factorisation runs in one warp with one column
+// per lane, and the product uses every thread.
+__device__ __forceinline__ void chol_body(const double* __restrict__ gram, int panels, int m,
+                                          const double* __restrict__ R1, double* __restrict__ Rout,
+                                          double* __restrict__ Rinv_out, int* __restrict__ status,
+                                          unsigned long long* chk) {
     __shared__ double G[32 * kLd];
-    __shared__ double R[32 * kLd];
-    const int tid = threadIdx.x;
+    __shared__ double R1s[32 * kLd];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = kRedThreads / 32;
     const int npair = m * (m + 1) / 2;
-    for (int e = tid; e < npair; e += blockDim.x) {
-        int q = e, i = 0;
-        while (q >= m - i) {
-            q -= m - i;
-            ++i;
-        }
-        const int j = i + q;
-        double s = 0.0;
-        for (int b = 0; b < panels; ++b)
-            if (GBN_IN(chk, 121, (int64_t)b * npair + e, (int64_t)panels * npair))
-                s += gram[(int64_t)b * npair + e];
-        if (GBN_IN(chk, 122, i * kLd + j, 32 * kLd)) G[i * kLd + j] = s;
-    }
-    for (int e = tid; e < 32 * kLd; e += blockDim.x) R[e] = 0.0;
+    for (int e = tid; e < 32 * kLd; e += blockDim.x) G[e] = 0.0;
+    if (R1)
+        for (int e = tid; e < m * m; e += blockDim.x) R1s[(e / m) * kLd + e % m] = R1[e];
     __syncthreads();
-    for (int j = 0; j < m; ++j) {
-        if (tid == 0) {
-            double d = G[j * kLd + j];
-            for (int i = 0; i < j; ++i) d -= R[i * kLd + j] * R[i * kLd + j];
-            if (d > 0.0) {
-                R[j * kLd + j] = sqrt(d);
-            } else {
-                R[j * kLd + j] = 0.0;  // column j lies in the span of the earlier ones
-                atomicOr(status, GBN_STATUS_RANK_DEFICIENT);
+    for (int e = warp; e < npair; e += nwarps) {
+        double s0 = 0.0, s1 = 0.0;
+        int b = lane;
+        for (; b + 32 < panels; b += 64) {
+            if (GBN_IN(chk, 121, (int64_t)(b + 32) * npair + e, (int64_t)panels * npair)) {
+                s0 += gram[(int64_t)b * npair + e];
+                s1 += gram[(int64_t)(b + 32) * npair + e];
             }
         }
-        __syncthreads();
-        const double rjj = R[j * kLd + j];
-        for (int l = j + 1 + tid; l < m; l += blockDim.x) {
-            double s = G[j * kLd + l];
-            for (int i = 0; i < j; ++i) s -= R[i * kLd + j] * R[i * kLd + l];
-            R[j * kLd + l] = (rjj != 0.0) ? s / rjj : 0.0;
+        if (b < panels && GBN_IN(chk, 122, (int64_t)b * npair + e, (int64_t)panels * npair))
+            s0 += gram[(int64_t)b * npair + e];
+        double s = s0 + s1;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            int q = e, i = 0;
+            while (q >= m - i) {
+                q -= m - i;
+                ++i;
+            }
+            if (GBN_IN(chk, 123, i * kLd + i + q, 32 * kLd)) G[i * kLd + i + q] = s;
         }
-        __syncthreads();
     }
+    __syncthreads();
+    if (warp == 0) {
+        // right-looking Cholesky, lane l owns column l; row j of R replaces row j of G
+        for (int j = 0; j < m; ++j) {
+            const double d = G[j * kLd + j];
+            const double rjj = d > 0.0 ? sqrt(d) : 0.0;
+            if (lane == 0 && !(d > 0.0)) atomicOr(status, GBN_STATUS_RANK_DEFICIENT);
+            __syncwarp();
+            if (lane >= j && lane < m)
+                G[j * kLd + lane] = (lane == j) ? rjj : (rjj != 0.0 ? G[j * kLd + lane] / rjj : 0.0);
+            __syncwarp();
+            if (lane > j && lane < m) {
+                const double rjl = G[j * kLd + lane];
+                for (int a = j + 1; a <= lane; ++a) G[a * kLd + lane] -= G[j * kLd + a] * rjl;
+            }
+            __syncwarp();
+        }
+        if (!R1 && Rinv_out && lane < m) {
+            // column `lane` of R^{-1} by back substitution (zero pivots give zero entries)
+            double x[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = 0.0;
+            for (int i = lane; i >= 0; --i) {
+                double s = (i == lane) ? 1.0 : 0.0;
+                for (int l = i + 1; l <= lane; ++l) s -= G[i * kLd + l] * x[l];
+                const double rii = G[i * kLd + i];
+                x[i] = rii != 0.0 ? s / rii : 0.0;
+            }
+            for (int i = 0; i < m; ++i)
+                if (GBN_IN(chk, 126, i * m + lane, m * m)) Rinv_out[i * m + lane] = (i <= lane) ? x[i] : 0.0;
+        }
+    }
+    __syncthreads();
     for (int e = tid; e < m * m; e += blockDim.x) {
         const int i = e / m, j = e % m;
         double v = 0.0;
         if (i <= j) {
             if (R1) {
-                for (int l = i; l <= j; ++l)
-                    if (GBN_IN(chk, 123, l * m + j, m * m)) v += R[i * kLd + l] * R1[l * m + j];
+                for (int l = i; l <= j; ++l) v = fma(G[i * kLd + l], R1s[l * kLd + j], v);
             } else {
-                v = R[i * kLd + j];
+                v = G[i * kLd + j];
             }
         }
-        if (GBN_IN(chk, 124, e, m * m)) Rout[e] = v;
+        if (GBN_IN(chk, 125, e, m * m)) Rout[e] = v;
     }
+}
+
+// Stage pointers of one dataset inside its workspace region.
+struct R0Ptrs {
+    double *colsum, *mu, *gram, *r1, *r1inv, *r0;
+    int* status;
+    unsigned long long* chk;
+};
+
+__device__ __host__ __forceinline__ R0Ptrs r0_ptrs(const Plan& p, char* ws) {
+    R0Ptrs q;
+    q.colsum = reinterpret_cast<double*>(ws + p.off_colsum);
+    q.mu = reinterpret_cast<double*>(ws + p.off_mu);
+    q.gram = reinterpret_cast<double*>(ws + p.off_gram);
+    q.r1 = reinterpret_cast<double*>(ws + p.off_r1);
+    q.r1inv = reinterpret_cast<double*>(ws + p.off_r1inv);
+    q.r0 = reinterpret_cast<double*>(ws + p.off_r0);
+    q.status = reinterpret_cast<int*>(ws + p.off_status);
+    q.chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
+    return q;
+}
+
+// One dataset: the plan travels as a kernel parameter.
+__global__ void colsum_kernel(const Plan p, const double* __restrict__ X, char* ws) {
+    const R0Ptrs q = r0_ptrs(p, ws);
+    colsum_body(blockIdx.x, X, p.n, p.m, p.rows_per_panel, q.colsum, p.panels, q.chk);
+}
+__global__ void __launch_bounds__(kRedThreads) mean_kernel(const Plan p, char* ws) {
+    const R0Ptrs q = r0_ptrs(p, ws);
+    mean_body(q.colsum, p.panels, p.m, p.n, p.center, p, q.mu, q.chk);
+}
+__global__ void gram_kernel(const Plan p, const double* __restrict__ X, char* ws, int pass) {
+    const R0Ptrs q = r0_ptrs(p, ws);
+    gram_body(blockIdx.x, X, p.n, p.m, p.rows_per_panel, q.mu, p.panels, pass ? q.r1inv : nullptr,
+              p, q.gram, q.chk);
+}
+__global__ void __launch_bounds__(kRedThreads) chol_kernel(const Plan p, char* ws, int pass) {
+    const R0Ptrs q = r0_ptrs(p, ws);
+    if (pass)
+        chol_body(q.gram, p.panels, p.m, q.r1, q.r0, nullptr, q.status, q.chk);
+    else
+        chol_body(q.gram, p.panels, p.m, nullptr, q.r1, q.r1inv, q.status, q.chk);
+}
+
+// A batch: blocks are mapped to (dataset, panel) through the prefix of panels.
+__global__ void status_clear_kernel_b(const BatchView v) {
+    const int d = blockIdx.x;
+    int* st = reinterpret_cast<int*>(v.ws[d] + v.plans[d].off_status);
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) st[i] = 0;
+}
+__global__ void colsum_kernel_b(const BatchView v) {
+    int64_t local;
+    const int d = batch_locate(v, v.panel_prefix, blockIdx.x, local);
+    const Plan& p = v.plans[d];
+    if (!p.center) return;
+    const R0Ptrs q = r0_ptrs(p, v.ws[d]);
+    colsum_body((int)local, v.X[d], p.n, p.m, p.rows_per_panel, q.colsum, p.panels, q.chk);
+}
+__global__ void __launch_bounds__(kRedThreads) mean_kernel_b(const BatchView v) {
+    const int d = blockIdx.x;
+    const Plan& p = v.plans[d];
+    const R0Ptrs q = r0_ptrs(p, v.ws[d]);
+    mean_body(q.colsum, p.panels, p.m, p.n, p.center, p, q.mu, q.chk);
+}
+__global__ void gram_kernel_b(const BatchView v, int pass) {
+    int64_t local;
+    const int d = batch_locate(v, v.panel_prefix, blockIdx.x, local);
+    const Plan& p = v.plans[d];
+    const R0Ptrs q = r0_ptrs(p, v.ws[d]);
+    gram_body((int)local, v.X[d], p.n, p.m, p.rows_per_panel, q.mu, p.panels,
+              pass ? q.r1inv : nullptr, p, q.gram, q.chk);
+}
+__global__ void __launch_bounds__(kRedThreads) chol_kernel_b(const BatchView v, int pass) {
+    const int d = blockIdx.x;
+    const Plan& p = v.plans[d];
+    const R0Ptrs q = r0_ptrs(p, v.ws[d]);
+    if (pass)
+        chol_body(q.gram, p.panels, p.m, q.r1, q.r0, nullptr, q.status, q.chk);
+    else
+        chol_body(q.gram, p.panels, p.m, nullptr, q.r1, q.r1inv, q.status, q.chk);
 }
 
 }  // namespace
 
 int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream) {
-    double* colsum = reinterpret_cast<double*>(ws + p.off_colsum);
-    double* gram = reinterpret_cast<double*>(ws + p.off_gram);
-    double* r1 = reinterpret_cast<double*>(ws + p.off_r1);
-    double* r0 = reinterpret_cast<double*>(ws + p.off_r0);
-    int* status = reinterpret_cast<int*>(ws + p.off_status);
-    unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
     if (cudaMemsetAsync(ws + p.off_status, 0, 256, stream) != cudaSuccess) return GBN_ERR_CUDA;
-    if (p.center)
-        colsum_kernel<<<p.panels, 256, 0, stream>>>(X, p.n, p.m, p.rows_per_panel, colsum, p.panels,
-                                                    chk);
-    gram_kernel<<<p.panels, 512, 0, stream>>>(X, p.n, p.m, p.rows_per_panel, colsum, p.panels,
-                                              p.center, nullptr, p, gram, chk);
-    chol_kernel<<<1, 256, 0, stream>>>(gram, p.panels, p.m, nullptr, r1, status, chk);
-    gram_kernel<<<p.panels, 512, 0, stream>>>(X, p.n, p.m, p.rows_per_panel, colsum, p.panels,
-                                              p.center, r1, p, gram, chk);
-    chol_kernel<<<1, 256, 0, stream>>>(gram, p.panels, p.m, r1, r0, status, chk);
+    if (p.center) colsum_kernel<<<p.panels, 256, 0, stream>>>(p, X, ws);
+    mean_kernel<<<1, kRedThreads, 0, stream>>>(p, ws);
+    gram_kernel<<<p.panels, 512, 0, stream>>>(p, X, ws, 0);
+    chol_kernel<<<1, kRedThreads, 0, stream>>>(p, ws, 0);
+    gram_kernel<<<p.panels, 512, 0, stream>>>(p, X, ws, 1);
+    chol_kernel<<<1, kRedThreads, 0, stream>>>(p, ws, 1);
+    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+}
+
+int launch_r0_batched(const BatchView& v, int64_t total_panels, cudaStream_t stream) {
+    const unsigned B = (unsigned)v.B, P = (unsigned)total_panels;
+    status_clear_kernel_b<<<B, 64, 0, stream>>>(v);
+    colsum_kernel_b<<<P, 256, 0, stream>>>(v);
+    mean_kernel_b<<<B, kRedThreads, 0, stream>>>(v);
+    gram_kernel_b<<<P, 512, 0, stream>>>(v, 0);
+    chol_kernel_b<<<B, kRedThreads, 0, stream>>>(v, 0);
+    gram_kernel_b<<<P, 512, 0, stream>>>(v, 1);
+    chol_kernel_b<<<B, kRedThreads, 0, stream>>>(v, 1);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 

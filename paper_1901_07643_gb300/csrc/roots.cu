@@ -150,9 +150,9 @@ __device__ void write_leaf(const Node<T>& nd, int ell, int Q, T* rec, int lane, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32) roots_kernel(const double* __restrict__ R0, Plan p,
-                                                   T* __restrict__ leaves,
-                                                   unsigned long long* chk) {
+__device__ __forceinline__ void roots_body(const double* __restrict__ R0, const Plan& p,
+                                           T* __restrict__ leaves, unsigned long long* chk,
+                                           uint64_t cta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Node<T>* nodes = reinterpret_cast<Node<T>*>(smem_raw);
     const int lane = threadIdx.x;
@@ -169,7 +169,6 @@ __global__ void __launch_bounds__(32) roots_kernel(const double* __restrict__ R0
         n0.nc = 0;
     }
     __syncwarp();
-    const uint64_t cta = blockIdx.x;
     int cur = 0;
     for (int j = 0; j < p.k - p.W; ++j) {
         if ((cta >> j) & 1ull)
@@ -178,7 +177,7 @@ __global__ void __launch_bounds__(32) roots_kernel(const double* __restrict__ R0
             node_exclude(nodes[cur], nodes[cur ^ 1], lane, chk);
         cur ^= 1;
     }
-    T* rec = leaves + (size_t)blockIdx.x * p.leaf_stride;
+    T* rec = leaves + (size_t)cta * p.leaf_stride;
     Node<T>* lvl[8];
     lvl[0] = &nodes[cur];
     for (int t = 1; t <= p.W; ++t) lvl[t] = &nodes[1 + t];
@@ -198,19 +197,52 @@ __global__ void __launch_bounds__(32) roots_kernel(const double* __restrict__ R0
 }
 
 template <typename T>
-int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
-    const double* r0 = reinterpret_cast<const double*>(ws + p.off_r0);
-    T* leaves = reinterpret_cast<T*>(ws + p.off_leaves);
-    unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
-    const size_t smem = sizeof(Node<T>) * (size_t)(p.W + 2);
-    static bool attr_set = false;
+__global__ void __launch_bounds__(32) roots_kernel(const Plan p, char* ws) {
+    roots_body<T>(reinterpret_cast<const double*>(ws + p.off_r0), p,
+                  reinterpret_cast<T*>(ws + p.off_leaves),
+                  reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset),
+                  blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32) roots_kernel_b(const BatchView v) {
+    int64_t local;
+    const int d = batch_locate(v, v.cta_prefix, blockIdx.x, local);
+    const Plan& p = v.plans[d];
+    char* ws = v.ws[d];
+    roots_body<T>(reinterpret_cast<const double*>(ws + p.off_r0), p,
+                  reinterpret_cast<T*>(ws + p.off_leaves),
+                  reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset),
+                  (uint64_t)local);
+}
+
+template <typename T>
+int set_roots_smem() {
+    static bool attr_set = false;  // per process; every device gets the same attribute value
     if (!attr_set) {
         if (cudaFuncSetAttribute(roots_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(Node<T>) * 7)) != cudaSuccess ||
+            cudaFuncSetAttribute(roots_kernel_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(Node<T>) * 7)) != cudaSuccess)
             return GBN_ERR_CUDA;
         attr_set = true;
     }
-    roots_kernel<T><<<(unsigned)p.n_cta, 32, smem, stream>>>(r0, p, leaves, chk);
+    return GBN_OK;
+}
+
+template <typename T>
+int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
+    if (set_roots_smem<T>()) return GBN_ERR_CUDA;
+    const size_t smem = sizeof(Node<T>) * (size_t)(p.W + 2);
+    roots_kernel<T><<<(unsigned)p.n_cta, 32, smem, stream>>>(p, ws);
+    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+}
+
+template <typename T>
+int launch_roots_batched_t(const BatchView& v, int64_t total_cta, int max_w, cudaStream_t stream) {
+    if (set_roots_smem<T>()) return GBN_ERR_CUDA;
+    const size_t smem = sizeof(Node<T>) * (size_t)(max_w + 2);
+    roots_kernel_b<T><<<(unsigned)total_cta, 32, smem, stream>>>(v);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
@@ -219,6 +251,12 @@ int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
 int launch_roots(const Plan& p, char* ws, cudaStream_t stream) {
     return p.precision ? launch_roots_t<double>(p, ws, stream)
                        : launch_roots_t<float>(p, ws, stream);
+}
+
+int launch_roots_batched(const BatchView& v, int64_t total_cta, int max_w, int precision,
+                         cudaStream_t stream) {
+    return precision ? launch_roots_batched_t<double>(v, total_cta, max_w, stream)
+                     : launch_roots_batched_t<float>(v, total_cta, max_w, stream);
 }
 
 }  // namespace gbn

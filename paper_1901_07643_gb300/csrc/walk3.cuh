@@ -73,6 +73,33 @@ struct WalkArgs {
     long long watchdog_ns;       // bound on every wait
 };
 
+// A wait inside the walk that lasts this long means the schedule is broken.
+constexpr long long kWatchdogNs = 2000000000ll;
+
+// Walk arguments of one dataset (host side).
+template <typename T>
+inline WalkArgs<T> make_walk_args(const Plan& p, char* ws, void* out) {
+    WalkArgs<T> a;
+    a.out = out;
+    a.leaves = reinterpret_cast<const T*>(ws + p.off_leaves);
+    a.leaf_stride = p.leaf_stride;
+    a.m = p.m;
+    a.k = p.k;
+    a.W = p.W;
+    a.lanes = p.lanes;
+    const double n = (double)p.n;
+    a.alpha = (T)(n * 0.69314718055994530942);
+    a.lnn = (T)log(n);
+    a.nlnn = (T)(n * log(n));
+    a.chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
+    a.timing = reinterpret_cast<unsigned long long*>(ws + p.off_status + kTimingOffset);
+    a.status = reinterpret_cast<int*>(ws + p.off_status);
+    a.out_size = (size_t)p.m << (p.m - 1);
+    a.n_cwarps = p.n_bwarps;
+    a.watchdog_ns = kWatchdogNs;
+    return a;
+}
+
 constexpr int kChunk = 16;  // tape steps per barrier
 
 // The swap sequence of Algorithm 1 with, per step, the 0-based swap row i
@@ -467,7 +494,7 @@ __constant__ StepTab<GBN_Q> c_steps = make_step_tab<GBN_Q>();
 constexpr int kMaxConsumerWarps = 8;
 
 template <typename T, int Q, bool COV>
-__global__ void __launch_bounds__(32 * (1 + kMaxConsumerWarps)) walk_kernel(WalkArgs<T> a) {
+__device__ __forceinline__ void walk_body(const WalkArgs<T>& a, uint64_t cta) {
     extern __shared__ __align__(16) unsigned char smem[];
     using S = Smem<T, Q>;
     static_assert(Q == GBN_Q, "one Q per translation unit");
@@ -477,13 +504,27 @@ __global__ void __launch_bounds__(32 * (1 + kMaxConsumerWarps)) walk_kernel(Walk
     if (threadIdx.x < S::chunks) mbar_init(&full[threadIdx.x], 1);
     for (int c = threadIdx.x + blockDim.x; c < S::chunks; c += blockDim.x) mbar_init(&full[c], 1);
     __syncthreads();
-    const uint64_t cta = blockIdx.x;
     const uint64_t Fhi = cta << a.W;
-    const T* rec = a.leaves + (size_t)blockIdx.x * a.leaf_stride;
+    const T* rec = a.leaves + (size_t)cta * a.leaf_stride;
     if (warp == 0)
         produce<T, Q>(a, c_steps, rec, smem, lane, lane < a.lanes);
     else
         consume<T, Q, COV>(a, rec, smem, lane, warp - 1, cta, Fhi);
+}
+
+template <typename T, int Q, bool COV>
+__global__ void __launch_bounds__(32 * (1 + kMaxConsumerWarps)) walk_kernel(const WalkArgs<T> a) {
+    walk_body<T, Q, COV>(a, blockIdx.x);
+}
+
+// A batch: the block finds its dataset through the prefix of sub-walk CTAs
+// and copies that dataset's arguments.
+template <typename T, int Q, bool COV>
+__global__ void __launch_bounds__(32 * (1 + kMaxConsumerWarps)) walk_kernel_b(const BatchView v) {
+    int64_t local;
+    const int d = batch_locate(v, v.cta_prefix, blockIdx.x, local);
+    const WalkArgs<T> a = static_cast<const WalkArgs<T>*>(v.walk_args)[d];
+    walk_body<T, Q, COV>(a, (uint64_t)local);
 }
 
 template <typename T, int Q, bool COV>
@@ -497,6 +538,17 @@ int launch_walk_q(const WalkArgs<T>& a, int64_t n_cta, cudaStream_t stream) {
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
+template <typename T, int Q, bool COV>
+int launch_walk_batched_q(const BatchView& v, int64_t total_cta, int n_cwarps, cudaStream_t stream) {
+    const size_t smem = Smem<T, Q>::bytes;
+    if (n_cwarps < 1 || n_cwarps > kMaxConsumerWarps) return GBN_ERR_Q;
+    if (cudaFuncSetAttribute(walk_kernel_b<T, Q, COV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return GBN_ERR_CUDA;
+    walk_kernel_b<T, Q, COV><<<(unsigned)total_cta, 32 * (1 + n_cwarps), smem, stream>>>(v);
+    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+}
+
 }  // namespace gbn
 #endif
 
@@ -505,3 +557,7 @@ int launch_walk_q(const WalkArgs<T>& a, int64_t n_cta, cudaStream_t stream) {
 #define GBN_WALK_INST_NAME(T, Q, COV) gbn_launch_walk_##T##_q##Q##_c##COV
 #define GBN_WALK_DECL(T, Q, COV) \
     int GBN_WALK_INST_NAME(T, Q, COV)(const gbn::WalkArgs<T>& a, int64_t n_cta, cudaStream_t s)
+#define GBN_WALK_B_INST_NAME(T, Q, COV) gbn_launch_walk_b_##T##_q##Q##_c##COV
+#define GBN_WALK_B_DECL(T, Q, COV)                                                          \
+    int GBN_WALK_B_INST_NAME(T, Q, COV)(const gbn::BatchView& v, int64_t total_cta, int nw, \
+                                        cudaStream_t s)

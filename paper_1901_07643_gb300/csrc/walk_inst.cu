@@ -12,3 +12,9 @@ int GBN_XNAME(GBN_T, GBN_Q, GBN_COV)(const gbn::WalkArgs<GBN_T>& a, int64_t n_ct
                                       cudaStream_t s) {
     return gbn::launch_walk_q<GBN_T, GBN_Q, (GBN_COV != 0)>(a, n_cta, s);
 }
+
+#define GBN_XBNAME(T, Q, C) GBN_WALK_B_INST_NAME(T, Q, C)
+int GBN_XBNAME(GBN_T, GBN_Q, GBN_COV)(const gbn::BatchView& v, int64_t total_cta, int nw,
+                                       cudaStream_t s) {
+    return gbn::launch_walk_batched_q<GBN_T, GBN_Q, (GBN_COV != 0)>(v, total_cta, nw, s);
+}

@@ -11,7 +11,15 @@ void dump() {
         std::printf("%d %u %u\n", Q, (unsigned)tab.row[t] + 1u, (unsigned)tab.pre[t]);
 }
 
+// upsilon_at (the run-time generator used by the adjoint walk): "U Q index"
+void dump_runtime(int Q) {
+    const long long n = (1ll << Q) - Q - 1;
+    for (long long t = 0; t < n; ++t) std::printf("U %d %d\n", Q, gbn::upsilon_at(Q, t));
+    std::printf("U %d %d\n", Q, gbn::upsilon_at(Q, n));  // past the end: 0
+}
+
 int main() {
+    for (int Q = 2; Q <= 14; ++Q) dump_runtime(Q);
     dump<2>(); dump<3>(); dump<4>(); dump<5>(); dump<6>(); dump<7>(); dump<8>();
     dump<9>(); dump<10>(); dump<11>(); dump<12>();
     return 0;

@@ -82,8 +82,12 @@ def test_device_swap_tables_match_greedy_swaps(tmp_path):
     src = os.path.join(ROOT, "tests", "native", "seq_dump.cu")
     subprocess.run([gbn_build._nvcc(), "-std=c++17", "--expt-relaxed-constexpr", "-o", str(exe),
                     src], check=True, capture_output=True)
-    rows = [list(map(int, ln.split())) for ln in
-            subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()]
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    rows = [list(map(int, ln.split())) for ln in lines if not ln.startswith("U ")]
+    run = [list(map(int, ln.split()[1:])) for ln in lines if ln.startswith("U ")]
+    for Q in range(2, 15):
+        got = [r[1] for r in run if r[0] == Q]
+        assert got == seq.greedy_swaps(Q) + [0]
     for Q in range(2, 13):
         mine = [r for r in rows if r[0] == Q]
         sw = seq.greedy_swaps(Q)
@@ -102,3 +106,45 @@ def test_noalloc_host_rejections(lib):
     assert f(None, 64, 31, None, None) == -1     # m out of range
     assert f(None, 5, 8, None, None) == -2       # n < m + 1
     assert f(None, 100, 12, None, None) == -3    # NULL pointers
+
+
+def test_batched_host_checks(lib):
+    """Batched sizing and argument checks run on the host (no device work)."""
+    import ctypes
+    B = 3
+    ns = (ctypes.c_int64 * B)(100, 50, 400)
+    ms = (ctypes.c_int32 * B)(12, 8, 20)
+    o = binding.Opts()
+    lib.givensbn_default_opts(ctypes.byref(o))
+    b = ctypes.c_size_t(0)
+    f = lib.givensbn_batched_workspace_size
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(binding.Opts),
+                  ctypes.POINTER(ctypes.c_size_t)]
+    assert f(ctypes.cast(ns, ctypes.c_void_p), ctypes.cast(ms, ctypes.c_void_p), B,
+             ctypes.byref(o), ctypes.byref(b)) == 0
+    singles = sum(binding.workspace_size(n, m, 0, 6) for n, m in zip(ns, ms))
+    assert b.value >= singles
+    assert f(ctypes.cast(ns, ctypes.c_void_p), ctypes.cast(ms, ctypes.c_void_p), 0,
+             ctypes.byref(o), ctypes.byref(b)) == -9
+    bad = (ctypes.c_int32 * B)(12, 1, 20)
+    assert f(ctypes.cast(ns, ctypes.c_void_p), ctypes.cast(bad, ctypes.c_void_p), B,
+             ctypes.byref(o), ctypes.byref(b)) == -1
+    g = lib.score_all_families_batched
+    g.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.POINTER(binding.Opts)]
+    assert g(None, ctypes.cast(ns, ctypes.c_void_p), ctypes.cast(ms, ctypes.c_void_p), B, None,
+             None, ctypes.byref(o)) == -3
+
+
+def test_backward_workspace_and_checks(lib):
+    import ctypes
+    assert binding.backward_workspace_size(2000, 16, 0, 0) > 0
+    o = binding.Opts()
+    lib.givensbn_default_opts(ctypes.byref(o))
+    f = lib.score_all_families_backward
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.POINTER(binding.Opts)]
+    assert f(None, 100, 12, None, None, ctypes.byref(o)) == -3
+    assert f(None, 100, 31, None, None, ctypes.byref(o)) == -1
+    o.q = 13
+    assert f(None, 100, 12, None, None, ctypes.byref(o)) == -7
