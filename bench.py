@@ -37,7 +37,7 @@ WALK_SOURCES = ["paper_1901_07643_gb300/csrc/walk3.cuh", "paper_1901_07643_gb300
                 "paper_1901_07643_gb300/csrc/walk_dispatch.cu",
                 "paper_1901_07643_gb300/csrc/gbn_internal.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk_traffic.json")
-LAUNCHES_PER_STEP = 8  # colsum, mean, gram x2, cholesky x2, roots, walk
+LAUNCHES_PER_STEP = 11  # colsum, mean, gram x2, cholesky x2, fix-up flags, roots, walk, fix-up scan + solve
 
 
 def _args():
@@ -245,13 +245,15 @@ def _time_steps(fn, steps, flush, stream):
     pairs = []
     for _ in range(steps):
         flush.zero_()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        fn(ev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev[4].record(stream)
+        fn(ev[:4])
+        ev[5].record(stream)
         pairs.append(ev)
     torch.cuda.synchronize()
     for ev in pairs:
-        step_ms.append(ev[0].elapsed_time(ev[3]))
-        walk_ms.append(ev[2].elapsed_time(ev[3]))
+        step_ms.append(ev[4].elapsed_time(ev[5]))   # the whole call
+        walk_ms.append(ev[2].elapsed_time(ev[3]))   # the walk kernel alone
     return step_ms, walk_ms
 
 

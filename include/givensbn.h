@@ -62,6 +62,8 @@ extern "C" {
 /* device status bits (givensbn_status) */
 #define GBN_STATUS_RANK_DEFICIENT 1 /* a Cholesky pivot was <= 0: RSS 0 for some families */
 #define GBN_STATUS_WATCHDOG 2       /* a bounded wait inside a kernel expired: output incomplete */
+#define GBN_STATUS_FIXUP_OVERFLOW 4 /* more ill-conditioned families than the fix-up list holds;
+                                       the rest keep their FP32 scores */
 
 #define GBN_MIN_M 2
 #define GBN_MAX_M 30
@@ -75,10 +77,14 @@ typedef struct givensbn_opts {
     void* workspace;        /* device scratch, >= givensbn_workspace_size() bytes, 256-byte aligned */
     size_t workspace_bytes;
     void* stage_events;     /* NULL, or host array of 4 cudaEvent_t recorded on the stream before
-                               the R0 stage, after it, after the sub-walk roots and after the walk */
+                               the R0 stage, after it, after the sub-walk roots and after the walk
+                               (before the FP64 fix-up pass) */
+    double fixup_tau;       /* FP32 walk only: a family whose RSS falls below fixup_tau times
+                               the child's centred sum of squares is recomputed in FP64 from R0
+                               (QR of its columns) and scored in FP64; 0 disables.  Default 1e-6 */
 } givensbn_opts;
 
-/* Default options: FP32, centring on, automatic q, no workspace. */
+/* Default options: FP32, centring on, automatic q, no workspace, fixup_tau 1e-6. */
 void givensbn_default_opts(givensbn_opts* opts);
 
 /*

@@ -20,6 +20,18 @@ _lock = threading.Lock()
 _lib = None
 
 GBN_STATUS_RANK_DEFICIENT = 1
+GBN_STATUS_WATCHDOG = 2
+GBN_STATUS_FIXUP_OVERFLOW = 4
+
+
+def _check_status(st: int) -> None:
+    if st & GBN_STATUS_WATCHDOG:
+        raise RuntimeError("givensbn: a bounded wait in the walk expired; the table is incomplete")
+    if st & GBN_STATUS_RANK_DEFICIENT:
+        warnings.warn("givensbn: data rank deficient; some RSS are 0 (scores -inf)")
+    if st & GBN_STATUS_FIXUP_OVERFLOW:
+        warnings.warn("givensbn: more ill-conditioned families than the FP64 fix-up list holds; "
+                      "the rest keep FP32 scores")
 
 
 class Opts(ctypes.Structure):
@@ -33,6 +45,7 @@ class Opts(ctypes.Structure):
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
         ("stage_events", ctypes.c_void_p),
+        ("fixup_tau", ctypes.c_double),
     ]
 
 
@@ -82,9 +95,11 @@ def auto_q(m: int, precision: int = 0) -> int:
 
 
 def _opts(precision=0, q=0, center=True, debug_coverage=False, stream=None,
-          workspace=None, stage_events=None) -> Opts:
+          workspace=None, stage_events=None, fixup_tau=None) -> Opts:
     o = Opts()
     load().givensbn_default_opts(ctypes.byref(o))
+    if fixup_tau is not None:
+        o.fixup_tau = float(fixup_tau)
     o.precision = int(precision)
     o.q = int(q)
     o.center = 1 if center else 0
@@ -101,8 +116,8 @@ def _opts(precision=0, q=0, center=True, debug_coverage=False, stream=None,
     return o
 
 
-def workspace_size(n: int, m: int, precision: int = 0, q: int = 0) -> int:
-    o = _opts(precision, q)
+def workspace_size(n: int, m: int, precision: int = 0, q: int = 0, fixup_tau=None) -> int:
+    o = _opts(precision, q, fixup_tau=fixup_tau)
     b = ctypes.c_size_t(0)
     rc = load().givensbn_workspace_size(n, m, ctypes.byref(o), ctypes.byref(b))
     if rc:
@@ -127,7 +142,7 @@ def _stream_handle(stream, device):
 def score_all_families(X: torch.Tensor, out: torch.Tensor | None = None, *, precision: int = 0,
                        q: int = 0, center: bool = True, debug_coverage: bool = False,
                        workspace: torch.Tensor | None = None, stream=None,
-                       stage_events=None, check: bool = True) -> torch.Tensor:
+                       stage_events=None, check: bool = True, fixup_tau=None) -> torch.Tensor:
     """Scores of all m * 2^(m-1) families of the n x m data X (CUDA float64, row-major).
 
     Returns a 1-D tensor in table layout (float32 for precision 0, float64 for
@@ -147,13 +162,14 @@ def score_all_families(X: torch.Tensor, out: torch.Tensor | None = None, *, prec
         else:
             out = torch.empty(size, dtype=torch.float64 if precision else torch.float32, device=dev)
     if workspace is None:
-        workspace = torch.empty(workspace_size(n, m, precision, q), dtype=torch.uint8, device=dev)
+        workspace = torch.empty(workspace_size(n, m, precision, q, fixup_tau), dtype=torch.uint8,
+                                device=dev)
     if stage_events is not None:
         for e in stage_events:  # torch creates the CUDA event on its first record()
             if not e.cuda_event:
                 e.record(stream if stream is not None else torch.cuda.current_stream(dev))
     o = _opts(precision, q, center, debug_coverage, _stream_handle(stream, dev), workspace,
-              stage_events)
+              stage_events, fixup_tau)
     rc = load().score_all_families(ctypes.c_void_p(X.data_ptr()), n, m,
                                    ctypes.c_void_p(out.data_ptr()), ctypes.byref(o))
     if rc:
@@ -163,8 +179,7 @@ def score_all_families(X: torch.Tensor, out: torch.Tensor | None = None, *, prec
         rc = load().givensbn_status(ctypes.byref(o), ctypes.byref(st))
         if rc:
             raise GivensBNError(rc)
-        if st.value & GBN_STATUS_RANK_DEFICIENT:
-            warnings.warn("givensbn: data rank deficient; some RSS are 0 (scores -inf)")
+        _check_status(st.value)
     return out
 
 

@@ -78,6 +78,13 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     off = align_up(off + sizeof(double) * (size_t)m * m, 256);
     p->off_leaves = off;
     off = align_up(off + es * p->leaf_stride * (size_t)p->n_cta, 256);
+    const double tau = opts ? opts->fixup_tau : 1e-6;
+    if (precision == 0 && !p->coverage && tau > 0.0) {
+        p->fix_cap = kFixCap;
+        p->fix_tau = tau;
+        p->off_fix = off;
+        off = align_up(off + 256 + sizeof(long long) * (size_t)kFixCap, 256);
+    }
     p->total_bytes = off;
     return GBN_OK;
 }
@@ -110,12 +117,38 @@ static int checked_stage(const char* name, int rc, const Plan& p, char* ws, cuda
     return rc;
 }
 
+namespace gbn {
+
+int run_pipeline(const Plan& p, const double* X, char* ws, void* out, cudaStream_t stream,
+                 void* stage_events) {
+    cudaEvent_t* ev = static_cast<cudaEvent_t*>(stage_events);
+    if (ev && cudaEventRecord(ev[0], stream) != cudaSuccess) return GBN_ERR_CUDA;
+    int rc = launch_r0(p, X, ws, stream);
+    if (rc == GBN_OK && p.fix_cap) rc = launch_fix_flags(p, ws, stream);
+    if ((rc = checked_stage("r0", rc, p, ws, stream))) return rc;
+    if (ev && cudaEventRecord(ev[1], stream) != cudaSuccess) return GBN_ERR_CUDA;
+    rc = launch_roots(p, ws, stream);
+    if ((rc = checked_stage("roots", rc, p, ws, stream))) return rc;
+    if (ev && cudaEventRecord(ev[2], stream) != cudaSuccess) return GBN_ERR_CUDA;
+    rc = launch_walk(p, ws, out, stream);
+    if ((rc = checked_stage("walk", rc, p, ws, stream))) return rc;
+    if (ev && cudaEventRecord(ev[3], stream) != cudaSuccess) return GBN_ERR_CUDA;
+    if (p.fix_cap) {
+        rc = launch_fixup(p, ws, out, stream);
+        if ((rc = checked_stage("fixup", rc, p, ws, stream))) return rc;
+    }
+    return GBN_OK;
+}
+
+}  // namespace gbn
+
 extern "C" {
 
 void givensbn_default_opts(givensbn_opts* opts) {
     if (!opts) return;
     memset(opts, 0, sizeof(*opts));
     opts->center = 1;
+    opts->fixup_tau = 1e-6;
 }
 
 int32_t givensbn_auto_q(int32_t m, int32_t precision) { return auto_q(m, precision); }
@@ -140,19 +173,8 @@ int score_all_families(const double* X, int64_t n, int32_t m, void* out_scores,
     if (!opts->workspace || opts->workspace_bytes < p.total_bytes) return GBN_ERR_WORKSPACE;
     if ((uintptr_t)opts->workspace & 255u) return GBN_ERR_ALIGN;
     char* ws = static_cast<char*>(opts->workspace);
-    cudaStream_t stream = static_cast<cudaStream_t>(opts->stream);
-    cudaEvent_t* ev = static_cast<cudaEvent_t*>(opts->stage_events);
-    if (ev && cudaEventRecord(ev[0], stream) != cudaSuccess) return GBN_ERR_CUDA;
-    rc = launch_r0(p, X, ws, stream);
-    if ((rc = checked_stage("r0", rc, p, ws, stream))) return rc;
-    if (ev && cudaEventRecord(ev[1], stream) != cudaSuccess) return GBN_ERR_CUDA;
-    rc = launch_roots(p, ws, stream);
-    if ((rc = checked_stage("roots", rc, p, ws, stream))) return rc;
-    if (ev && cudaEventRecord(ev[2], stream) != cudaSuccess) return GBN_ERR_CUDA;
-    rc = launch_walk(p, ws, out_scores, stream);
-    if ((rc = checked_stage("walk", rc, p, ws, stream))) return rc;
-    if (ev && cudaEventRecord(ev[3], stream) != cudaSuccess) return GBN_ERR_CUDA;
-    return GBN_OK;
+    return run_pipeline(p, X, ws, out_scores, static_cast<cudaStream_t>(opts->stream),
+                        opts->stage_events);
 }
 
 int givensbn_status(const givensbn_opts* opts, int32_t* status) {

@@ -65,6 +65,7 @@ int plan_batch(const int64_t* ns, const int32_t* ms, int32_t B, const givensbn_o
         }
     }
     o.q = Q;
+    o.fixup_tau = 0.0;  // the FP64 fix-up pass belongs to the single-dataset entry point
     L->plans.resize(B);
     for (int b = 0; b < B; ++b) {
         const int rc = make_plan(ns[b], ms[b], &o, &L->plans[b]);

@@ -31,6 +31,8 @@ namespace gbn {
 
 constexpr int kCheckOffset = 64;    // byte offset of the check record in the status block
 constexpr int kTimingOffset = 128;  // byte offset of the timing counters (timing builds)
+constexpr int kFixCountOffset = 16; // byte offset of the fix-up list length (unsigned)
+constexpr int kFixCap = 1 << 18;    // fix-up list capacity (families)
 
 constexpr int kMaxQ = 9;     // largest sub-walk size compiled (FP32; the tape lives in shared memory)
 constexpr int kMaxQFp64 = 8; // FP64: the register-resident block is twice as large
@@ -60,6 +62,9 @@ struct Plan {
     size_t off_status = 0, off_colsum = 0, off_mu = 0, off_gram = 0, off_r1 = 0, off_r1inv = 0;
     size_t off_r0 = 0;
     size_t off_leaves = 0;
+    size_t off_fix = 0;      // fix-up: [mask (u32) | pad | thr float[32]] then the slot list
+    int fix_cap = 0;         // 0: no fix-up (FP64 walk, coverage mode or fixup_tau == 0)
+    double fix_tau = 0.0;
     size_t total_bytes = 0;
     size_t leaf_stride = 0;  // elements per CTA leaf record
     int n_bwarps = 1;        // consumer warps per walk CTA (they loop over the CTA's columns)
@@ -72,6 +77,13 @@ int auto_q(int m, int precision);
 int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream);
 int launch_roots(const Plan& p, char* ws, cudaStream_t stream);
 int launch_walk(const Plan& p, char* ws, void* out, cudaStream_t stream);
+// Ill-conditioned families (FP32 walk): flag the variables whose smallest
+// possible RSS is tiny before the walk, recompute the listed families after it.
+int launch_fix_flags(const Plan& p, char* ws, cudaStream_t stream);
+int launch_fixup(const Plan& p, char* ws, void* out, cudaStream_t stream);
+// The whole single-dataset pipeline (R0, flags, roots, walk, fix-up).
+int run_pipeline(const Plan& p, const double* X, char* ws, void* out, cudaStream_t stream,
+                 void* stage_events);
 
 // The t-th swap (0-based t, 1-based swap index in [1, Q-1]) of the greedy
 // sequence Upsilon(Q) of Algorithm 1, read as

@@ -69,8 +69,5 @@ extern "C" int score_all_families_noalloc(const double* X, int64_t n, int32_t m,
     if (((uintptr_t)X & 7u) || ((uintptr_t)out_scores & 15u)) return GBN_ERR_ALIGN;
     char* ws = nullptr;
     if ((rc = scratch_for_current_device(&ws))) return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if ((rc = launch_r0(p, X, ws, s))) return rc;
-    if ((rc = launch_roots(p, ws, s))) return rc;
-    return launch_walk(p, ws, out_scores, s);
+    return run_pipeline(p, X, ws, out_scores, static_cast<cudaStream_t>(stream), nullptr);
 }
