@@ -97,9 +97,12 @@ int givensbn_workspace_size(int64_t n, int32_t m, const givensbn_opts* opts, siz
  * Scores of every family of the n x m data X (the problem of Sec. 1;
  * method of Sec. 1.3, Sec. 3 and Sec. 6).
  *   X          device, n x m FP64 row-major, read only
- *   out_scores device, m * 2^(m-1) elements: float (precision 0) or double
- *              (precision 1), or uint32 counters if opts->debug_coverage;
- *              every element is written exactly once
+ *   out_scores device-accessible, m * 2^(m-1) elements: float (precision 0)
+ *              or double (precision 1), or uint32 counters if
+ *              opts->debug_coverage; every element is written exactly once
+ *              (the FP64 fix-up may write a listed element a second time).
+ *              Device memory, or pinned host memory (unified addressing): the
+ *              kernels then store the table straight into host memory.
  *   opts       host; workspace required
  */
 int score_all_families(const double* X, int64_t n, int32_t m, void* out_scores,

@@ -146,7 +146,8 @@ def score_all_families(X: torch.Tensor, out: torch.Tensor | None = None, *, prec
     """Scores of all m * 2^(m-1) families of the n x m data X (CUDA float64, row-major).
 
     Returns a 1-D tensor in table layout (float32 for precision 0, float64 for
-    precision 1, int32 counters for debug_coverage).  check=True synchronises
+    precision 1, int32 counters for debug_coverage).  `out` may be a pinned host
+    tensor: the kernels then write the table straight into host memory.  check=True synchronises
     and warns if the data were rank deficient.  stage_events: four
     torch.cuda.Event(enable_timing=True) recorded at the stage boundaries.
     """
@@ -161,6 +162,8 @@ def score_all_families(X: torch.Tensor, out: torch.Tensor | None = None, *, prec
             out = torch.zeros(size, dtype=torch.int32, device=dev)
         else:
             out = torch.empty(size, dtype=torch.float64 if precision else torch.float32, device=dev)
+    elif not (out.device == dev or (out.device.type == "cpu" and out.is_pinned())):
+        raise ValueError("out must be on X's device or in pinned host memory")
     if workspace is None:
         workspace = torch.empty(workspace_size(n, m, precision, q, fixup_tau), dtype=torch.uint8,
                                 device=dev)

@@ -220,7 +220,7 @@ extern "C" int score_all_families_batched(const double* const* Xs, const int64_t
     v.out = reinterpret_cast<void* const*>(base + L.off_out);
     v.walk_args = base + L.off_args;
     if ((rc = launch_r0_batched(v, L.total_panels, stream))) return rc;
-    if ((rc = launch_roots_batched(v, L.total_cta, L.maxW, precision, stream))) return rc;
+    if ((rc = launch_roots_batched(v, L.total_cta, L.Q, L.maxW, precision, stream))) return rc;
     return launch_walk_batched(v, L.total_cta, L.Q, precision, opts->debug_coverage != 0,
                                L.n_cwarps, stream);
 }

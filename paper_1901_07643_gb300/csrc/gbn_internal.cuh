@@ -139,7 +139,7 @@ __device__ __forceinline__ int batch_locate(const BatchView& v, const int64_t* p
 }
 
 int launch_r0_batched(const BatchView& v, int64_t total_panels, cudaStream_t stream);
-int launch_roots_batched(const BatchView& v, int64_t total_cta, int max_w, int precision,
+int launch_roots_batched(const BatchView& v, int64_t total_cta, int Q, int max_w, int precision,
                          cudaStream_t stream);
 int launch_walk_batched(const BatchView& v, int64_t total_cta, int Q, int precision, bool coverage,
                         int n_cwarps, cudaStream_t stream);

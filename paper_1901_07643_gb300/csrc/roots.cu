@@ -11,15 +11,20 @@
 // The roots are built as a binary tree over the fixed variables (the same
 // recursion as Algorithm 2, one level per fixed variable), starting from R0
 // whose column order puts the fixed variables first.  At each level the first
-// remaining variable either joins F -- drop the first row and column, since
-// the rest of R is already the factor of the remaining columns after
-// projecting it out -- or joins B -- delete its column, re-triangularise the
-// remaining upper-Hessenberg block with one Givens rotation per row pair, and
-// carry the deleted column along as a vector rotated with the rest.
+// undecided variable either joins F -- drop the first row, since the rest of
+// R is already the factor of the remaining columns after projecting it out --
+// or joins B -- its column leaves the triangle, the remaining upper-Hessenberg
+// block is re-triangularised with one Givens rotation per row pair, the
+// deleted column is carried along (rotated with the rest) and the row that
+// falls off the bottom is added to its residual.
 //
-// One warp per CTA of the walk: it follows its CTA's path through the k - W
-// top levels, then enumerates the 2^W leaves of the last W levels depth first
-// and writes them, lane-interleaved, to the leaf record the walk reads.
+// One warp per CTA of the walk; lane l owns column l of R0 (plan order) for
+// the whole tree and keeps it in registers: columns never move, deciding a
+// variable only changes the lane's role (undecided / in F / carried in B)
+// and drops one row.  The warp follows its CTA's path through the k - W top
+// levels, then enumerates the 2^W leaves of the last W levels depth first,
+// saving each level's node in shared memory to restart from it, and writes
+// every leaf, lane-interleaved, into the leaf record the walk reads.
 #include <math.h>
 
 #include "gbn_internal.cuh"
@@ -27,126 +32,111 @@
 namespace gbn {
 namespace {
 
-constexpr int kNodeLd = 32;  // row stride of a node matrix
-
-// Node matrices are flat arrays indexed [row * kNodeLd + column]: with this
-// toolchain, runtime-indexed two-dimensional shared-memory arrays were
-// mis-addressed in sm_103 code while flat ones were not.
-template <typename T>
-struct Node {
-    T M[32 * kNodeLd];  // row-major; columns [0,p) = R, [p, p+nc) = carried vectors
-    T C[32];      // residual of each carried column below row p
-    int var[32];  // variable of each column
-    int p, nc;
-};
+constexpr int kMaxRows = 32;
 
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
+// Include: the front variable joins F.  Drop row 0 (all lanes shift their rows).
 template <typename T>
-__device__ __forceinline__ void givens(T a, T b, T& c, T& s, T& rho) {
-    const T rho2 = a * a + b * b;
-    if (rho2 > T(0)) {
-        const T inv = rsqrt_t(rho2);
-        c = a * inv;
-        s = b * inv;
-        rho = rho2 * inv;
-    } else {
-        c = T(1);
-        s = T(0);
-        rho = T(0);
-    }
+__device__ __forceinline__ void drop_first_row(T (&M)[kMaxRows]) {
+#pragma unroll
+    for (int r = 0; r + 1 < kMaxRows; ++r) M[r] = M[r + 1];
+    M[kMaxRows - 1] = T(0);
 }
 
-// Child where the first variable joins the front set F.
+// Exclude: the column at lane `front` leaves the triangle (it is carried from
+// now on); rows 0 .. p-1 of the live columns front+1 .. front+p-1 are
+// re-triangularised, every lane applying the same rotations to its column;
+// carried lanes add the dropped bottom row p-1 to their residual.
 template <typename T>
-__device__ void node_include(const Node<T>& s, Node<T>& d, int lane, unsigned long long* chk) {
-    const int p = s.p, nc = s.nc;
-    const int ncol = p - 1 + nc;
-    if (lane < ncol && GBN_IN(chk, 201, lane + 1, 32) && GBN_IN(chk, 202, p, 33)) {
-        for (int r = 0; r < p - 1; ++r) d.M[(r) * kNodeLd + (lane)] = s.M[(r + 1) * kNodeLd + (lane + 1)];
-        d.C[lane] = s.C[lane + 1];
-        d.var[lane] = s.var[lane + 1];
-    }
-    if (lane == 0) {
-        d.p = p - 1;
-        d.nc = nc;
-    }
-    __syncwarp();
-}
-
-// Child where the first variable joins the back set B.
-template <typename T>
-__device__ void node_exclude(const Node<T>& s, Node<T>& d, int lane, unsigned long long* chk) {
-    const int p = s.p, nc = s.nc;
-    const int ncol = p + nc;
-    if (!GBN_IN(chk, 211, ncol, 33) || !GBN_IN(chk, 212, p, 33) || !GBN_IN(chk, 213, p - 1, 32)) {
-        __syncwarp();
-        return;
-    }
-    if (lane < ncol) {
-        const int src = (lane < ncol - 1) ? lane + 1 : 0;
-        for (int r = 0; r < p; ++r) d.M[(r) * kNodeLd + (lane)] = s.M[(r) * kNodeLd + (src)];
-        d.C[lane] = (lane < ncol - 1) ? s.C[src] : T(0);
-        d.var[lane] = s.var[src];
-    }
-    __syncwarp();
-    for (int j = 0; j + 1 < p; ++j) {
-        const T a = d.M[(j) * kNodeLd + (j)], b = d.M[(j + 1) * kNodeLd + (j)];
-        T c, sn, rho;
-        givens(a, b, c, sn, rho);
-        T x = T(0), y = T(0);
-        if (lane < ncol) {
-            x = d.M[(j) * kNodeLd + (lane)];
-            y = d.M[(j + 1) * kNodeLd + (lane)];
-        }
-        __syncwarp();
-        if (lane < ncol) {
-            T nx = c * x + sn * y, ny = c * y - sn * x;
-            if (lane == j) {
-                nx = rho;
-                ny = T(0);
+__device__ __forceinline__ void exclude_front(T (&M)[kMaxRows], T& C, int lane, int front, int p,
+                                              bool carried) {
+#pragma unroll
+    for (int j = 0; j + 1 < kMaxRows; ++j) {
+        if (j + 1 < p) {
+            const int piv = front + 1 + j;
+            const T a = __shfl_sync(0xffffffffu, M[j], piv);
+            const T b = __shfl_sync(0xffffffffu, M[j + 1], piv);
+            const T r2 = a * a + b * b;
+            T c = T(1), s = T(0), rho = T(0);
+            if (r2 > T(0)) {
+                const T inv = rsqrt_t(r2);
+                c = a * inv;
+                s = b * inv;
+                rho = r2 * inv;
             }
-            d.M[(j) * kNodeLd + (lane)] = nx;
-            d.M[(j + 1) * kNodeLd + (lane)] = ny;
+            const T x = M[j], y = M[j + 1];
+            M[j] = (lane == piv) ? rho : c * x + s * y;
+            M[j + 1] = (lane == piv) ? T(0) : c * y - s * x;
         }
-        __syncwarp();
     }
-    if (lane < ncol) {
-        if (lane >= p - 1) {
-            const T y = d.M[(p - 1) * kNodeLd + (lane)];
-            d.C[lane] += y * y;
+    // the bottom row p-1 falls off: into the residual of carried columns
+#pragma unroll
+    for (int r = 0; r < kMaxRows; ++r) {
+        if (r == p - 1) {
+            if (carried) C = fma(M[r], M[r], C);
+            M[r] = T(0);
         }
-        d.M[(p - 1) * kNodeLd + (lane)] = T(0);
     }
-    if (lane == 0) {
-        d.p = p - 1;
-        d.nc = nc + 1;
-    }
-    __syncwarp();
 }
 
 template <typename T>
-__device__ void write_leaf(const Node<T>& nd, int ell, int Q, T* rec, int lane, size_t stride,
-                           unsigned long long* chk) {
-    const int LQ = Q * (Q + 1) / 2;
-    for (int e = lane; e < LQ; e += 32) {
-        int pc = 0;
-        while ((pc + 1) * (pc + 2) / 2 <= e) ++pc;
-        const int r = e - pc * (pc + 1) / 2;
-        if (GBN_IN(chk, 221, (size_t)e * 32 + ell, stride) && GBN_IN(chk, 222, r * 32 + pc, 1024))
-            rec[(size_t)e * 32 + ell] = nd.M[(r) * kNodeLd + (pc)];
+__device__ __forceinline__ void decide(T (&M)[kMaxRows], T& C, unsigned& carried_mask, int lane,
+                                       int front, int p, bool include) {
+    if (include) {
+        drop_first_row(M);
+    } else {
+        carried_mask |= 1u << front;
+        exclude_front(M, C, lane, front, p, (carried_mask >> lane) & 1u);
     }
-    const int nc = nd.nc;
-    for (int e = lane; e < nc * (Q + 1); e += 32) {
-        const int col = Q + e / (Q + 1), row = e % (Q + 1);
-        if (!GBN_IN(chk, 223, col, 32)) continue;
-        const int v = nd.var[col];
-        const T val = (row < Q) ? nd.M[(row) * kNodeLd + (col)] : nd.C[col];
-        if (GBN_IN(chk, 224, (size_t)(LQ + v * (Q + 1) + row) * 32 + ell, stride))
-            rec[(size_t)(LQ + v * (Q + 1) + row) * 32 + ell] = val;
+}
+
+// Save / restore the lane's rows 0 .. rows-1 and residual (shared memory,
+// [slot][row][lane], conflict-free).
+// A slot holds `rows` rows and then the residual: (rows + 1) x 32 elements.
+template <typename T>
+__device__ __forceinline__ void save_node(T* st, const T (&M)[kMaxRows], T C, int lane, int rows) {
+#pragma unroll
+    for (int r = 0; r < kMaxRows; ++r)
+        if (r < rows) st[r * 32 + lane] = M[r];
+    st[rows * 32 + lane] = C;
+}
+template <typename T>
+__device__ __forceinline__ void load_node(const T* st, T (&M)[kMaxRows], T& C, int lane, int rows) {
+#pragma unroll
+    for (int r = 0; r < kMaxRows; ++r) M[r] = (r < rows) ? st[r * 32 + lane] : T(0);
+    C = st[rows * 32 + lane];
+}
+
+// Leaf record of sub-walk ell (lane-interleaved, see gbn_internal.cuh).
+template <typename T>
+__device__ __forceinline__ void write_leaf(const T (&M)[kMaxRows], T C, const Plan& p, int lane,
+                                           unsigned carried_mask, int ell, T* rec,
+                                           unsigned long long* chk) {
+    const int Q = p.Q, k = p.k, LQ = Q * (Q + 1) / 2;
+    if (lane >= k && lane < p.m) {  // L column i: rows 0 .. i of the L block
+        const int i = lane - k;
+#pragma unroll
+        for (int r = 0; r < kMaxRows; ++r) {
+            if (r <= i) {
+                const size_t ix = (size_t)(i * (i + 1) / 2 + r) * 32 + ell;
+                if (GBN_IN(chk, 221, ix, p.leaf_stride)) rec[ix] = M[r];
+            }
+        }
+    } else if (lane < k && ((carried_mask >> lane) & 1u)) {  // fixed variable in B
+        const int v = p.order[lane];
+        const size_t b0 = (size_t)(LQ + v * (Q + 1)) * 32 + ell;
+#pragma unroll
+        for (int r = 0; r < kMaxRows; ++r) {
+            if (r < Q) {
+                const size_t ix = b0 + (size_t)r * 32;
+                if (GBN_IN(chk, 224, ix, p.leaf_stride)) rec[ix] = M[r];
+            }
+        }
+        const size_t ix = b0 + (size_t)Q * 32;
+        if (GBN_IN(chk, 225, ix, p.leaf_stride)) rec[ix] = C;
     }
-    __syncwarp();
 }
 
 template <typename T>
@@ -154,44 +144,41 @@ __device__ __forceinline__ void roots_body(const double* __restrict__ R0, const 
                                            T* __restrict__ leaves, unsigned long long* chk,
                                            uint64_t cta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Node<T>* nodes = reinterpret_cast<Node<T>*>(smem_raw);
-    const int lane = threadIdx.x;
+    T* stack = reinterpret_cast<T*>(smem_raw);  // W slots of (Q + W + 1) x 32
+    const int lane = threadIdx.x & 31;
     const int m = p.m;
-    Node<T>& n0 = nodes[0];
-    if (lane < m) {
-        for (int r = 0; r < m; ++r)
-            if (GBN_IN(chk, 231, r * 32 + lane, 1024)) n0.M[(r) * kNodeLd + (lane)] = (T)R0[r * m + lane];
-        n0.C[lane] = T(0);
-        n0.var[lane] = p.order[lane];
-    }
-    if (lane == 0) {
-        n0.p = m;
-        n0.nc = 0;
-    }
-    __syncwarp();
-    int cur = 0;
-    for (int j = 0; j < p.k - p.W; ++j) {
-        if ((cta >> j) & 1ull)
-            node_include(nodes[cur], nodes[cur ^ 1], lane, chk);
-        else
-            node_exclude(nodes[cur], nodes[cur ^ 1], lane, chk);
-        cur ^= 1;
-    }
+    T M[kMaxRows];
+#pragma unroll
+    for (int r = 0; r < kMaxRows; ++r)
+        M[r] = (r < m && lane < m && GBN_IN(chk, 231, r * m + lane, m * m)) ? (T)R0[r * m + lane]
+                                                                         : T(0);
+    T C = T(0);
+    unsigned carried = 0u;
+    int front = 0;
+    for (; front < p.k - p.W; ++front)
+        decide(M, C, carried, lane, front, m - front, ((cta >> front) & 1ull) != 0ull);
     T* rec = leaves + (size_t)cta * p.leaf_stride;
-    Node<T>* lvl[8];
-    lvl[0] = &nodes[cur];
-    for (int t = 1; t <= p.W; ++t) lvl[t] = &nodes[1 + t];
+    const int top = front;
+    const unsigned carried_top = carried;
+    const size_t slot = (size_t)(p.Q + p.W + 1) * 32;  // rows at level t: Q + W - t
+    unsigned carried_at[8];
     int prev = 0;
     for (int lam = 0; lam < p.lanes; ++lam) {
         const int ell = (p.W > 0) ? (int)(__brev((unsigned)lam) >> (32 - p.W)) : 0;
         const int t0 = (lam == 0) ? 0 : __ffs(ell ^ prev) - 1;
-        for (int t = t0; t < p.W; ++t) {
-            if ((ell >> t) & 1)
-                node_include(*lvl[t], *lvl[t + 1], lane, chk);
-            else
-                node_exclude(*lvl[t], *lvl[t + 1], lane, chk);
+        if (lam > 0) {
+            load_node(stack + (size_t)t0 * slot, M, C, lane, m - top - t0);
+            carried = carried_at[t0];
+        } else {
+            carried = carried_top;
         }
-        write_leaf(*lvl[p.W], ell, p.Q, rec, lane, p.leaf_stride, chk);
+        for (int t = t0; t < p.W; ++t) {
+            const int rows = m - top - t;
+            save_node(stack + (size_t)t * slot, M, C, lane, rows);
+            carried_at[t] = carried;
+            decide(M, C, carried, lane, top + t, rows, ((ell >> t) & 1) != 0);
+        }
+        write_leaf(M, C, p, lane, carried, ell, rec, chk);
         prev = ell;
     }
 }
@@ -217,13 +204,19 @@ __global__ void __launch_bounds__(32) roots_kernel_b(const BatchView v) {
 }
 
 template <typename T>
+size_t roots_smem(int Q, int W) {
+    return sizeof(T) * (size_t)(Q + W + 1) * 32 * (size_t)(W > 0 ? W : 1);
+}
+
+template <typename T>
 int set_roots_smem() {
     static bool attr_set = false;  // per process; every device gets the same attribute value
     if (!attr_set) {
+        const int bytes = (int)roots_smem<T>(kMaxRows, kLaneBits);
         if (cudaFuncSetAttribute(roots_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(Node<T>) * 7)) != cudaSuccess ||
+                                 bytes) != cudaSuccess ||
             cudaFuncSetAttribute(roots_kernel_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(Node<T>) * 7)) != cudaSuccess)
+                                 bytes) != cudaSuccess)
             return GBN_ERR_CUDA;
         attr_set = true;
     }
@@ -233,16 +226,15 @@ int set_roots_smem() {
 template <typename T>
 int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
     if (set_roots_smem<T>()) return GBN_ERR_CUDA;
-    const size_t smem = sizeof(Node<T>) * (size_t)(p.W + 2);
-    roots_kernel<T><<<(unsigned)p.n_cta, 32, smem, stream>>>(p, ws);
+    roots_kernel<T><<<(unsigned)p.n_cta, 32, roots_smem<T>(p.Q, p.W), stream>>>(p, ws);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
 template <typename T>
-int launch_roots_batched_t(const BatchView& v, int64_t total_cta, int max_w, cudaStream_t stream) {
+int launch_roots_batched_t(const BatchView& v, int64_t total_cta, int Q, int max_w,
+                           cudaStream_t stream) {
     if (set_roots_smem<T>()) return GBN_ERR_CUDA;
-    const size_t smem = sizeof(Node<T>) * (size_t)(max_w + 2);
-    roots_kernel_b<T><<<(unsigned)total_cta, 32, smem, stream>>>(v);
+    roots_kernel_b<T><<<(unsigned)total_cta, 32, roots_smem<T>(Q, max_w), stream>>>(v);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
@@ -253,10 +245,10 @@ int launch_roots(const Plan& p, char* ws, cudaStream_t stream) {
                        : launch_roots_t<float>(p, ws, stream);
 }
 
-int launch_roots_batched(const BatchView& v, int64_t total_cta, int max_w, int precision,
+int launch_roots_batched(const BatchView& v, int64_t total_cta, int Q, int max_w, int precision,
                          cudaStream_t stream) {
-    return precision ? launch_roots_batched_t<double>(v, total_cta, max_w, stream)
-                     : launch_roots_batched_t<float>(v, total_cta, max_w, stream);
+    return precision ? launch_roots_batched_t<double>(v, total_cta, Q, max_w, stream)
+                     : launch_roots_batched_t<float>(v, total_cta, Q, max_w, stream);
 }
 
 }  // namespace gbn

@@ -205,3 +205,13 @@ def test_scale_invariance_of_shape():
     s1 = _gpu(X, precision=1).cpu().numpy()
     s2 = _gpu(X * a, precision=1).cpu().numpy()
     np.testing.assert_allclose(s2 - s1, 400 * math.log(a * a), rtol=0, atol=1e-8)
+
+
+def test_table_written_straight_to_pinned_host_memory():
+    X = synthetic.sem_sample(14, 300, 0.3, 1400)
+    Xt = torch.from_numpy(X).cuda()
+    dev = binding.score_all_families(Xt)
+    host = torch.empty(14 << 13, dtype=torch.float32, pin_memory=True)
+    binding.score_all_families(Xt, host)
+    torch.cuda.synchronize()
+    assert torch.equal(host, dev.cpu())
