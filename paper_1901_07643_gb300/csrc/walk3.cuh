@@ -156,6 +156,19 @@ __device__ __forceinline__ double2 wk_pair(double a, double b) { return make_dou
 template <typename T, bool COV>
 using OutT = typename std::conditional<COV, unsigned, T>::type;
 
+__device__ __forceinline__ void st_pred(float* addr, float v, bool on) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.global.f32 [%0], %1;\n\t}"
+        :
+        : "l"(addr), "f"(v), "r"((unsigned)on));
+}
+__device__ __forceinline__ void st_pred(double* addr, double v, bool on) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.global.f64 [%0], %1;\n\t}"
+        :
+        : "l"(addr), "d"(v), "r"((unsigned)on));
+}
+
 // Store at p + off (p: a per-thread pointer into the table, off < 2^32) when
 // `on`.  The score is computed unconditionally; only the store is predicated.
 template <typename T, bool COV>
@@ -167,9 +180,13 @@ __device__ __forceinline__ void emit_ptr(const WalkArgs<T>& a, OutT<T, COV>* p, 
             atomicAdd(p + off, 1u);
     } else {
         const T v = fma(a.alpha, wk_log2(rss), pen);
+#ifdef GBN_CHECKED
         if (on && GBN_IN(a.chk, 302,
                          (size_t)(p - reinterpret_cast<OutT<T, COV>*>(a.out)) + off, a.out_size))
             p[off] = v;
+#else
+        st_pred(p + off, v, on);  // a predicated store, never a branch around it
+#endif
     }
 }
 
