@@ -12,11 +12,12 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 static int max_q(int precision) { return precision ? kMaxQFp64 : kMaxQ; }
 
 int auto_q(int m, int precision) {
-    // Large sub-walks amortise their roots; the tape of one sub-walk tile
-    // (2^Q - Q - 1 steps) stays in shared memory, so Q <= 8 keeps several
-    // tiles resident per SM.
+    // Small sub-walks keep the walk's unrolled code small (its instruction
+    // fetch is what bounds it), large ones need fewer roots; the tape of one
+    // sub-walk (2^Q - Q - 1 steps) stays in shared memory.  At m = 26 on a
+    // GB300 the whole call took 2.65 / 2.59 / 2.66 ms for Q = 6 / 7 / 8.
     (void)precision;
-    int q = m - 18;
+    int q = m - 19;
     if (q < 6) q = 6;
     if (q > 8) q = 8;
     if (q > max_q(precision)) q = max_q(precision);
@@ -42,7 +43,7 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     p->n_cta = (int64_t)1 << (p->k - p->W);
     int pos = 0;
     for (int v = p->W; v < p->k; ++v) p->order[pos++] = v;
-    for (int v = 0; v < p->W; ++v) p->order[pos++] = v;
+    for (int v = p->W - 1; v >= 0; --v) p->order[pos++] = v;
     for (int v = p->k; v < m; ++v) p->order[pos++] = v;
     int panels = (int)(n / 32);
     if (panels < 1) panels = 1;
@@ -78,6 +79,8 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     off = align_up(off + sizeof(double) * (size_t)m * m, 256);
     p->off_leaves = off;
     off = align_up(off + es * p->leaf_stride * (size_t)p->n_cta, 256);
+    p->off_top = off;
+    off = align_up(off + top_node_bytes(*p), 256);
     const double tau = opts ? opts->fixup_tau : 1e-6;
     if (precision == 0 && !p->coverage && tau > 0.0) {
         p->fix_cap = kFixCap;

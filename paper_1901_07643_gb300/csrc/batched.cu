@@ -41,6 +41,7 @@ struct BatchLayout {
     size_t table_bytes = 0;             // device table at the workspace head
     size_t total = 0;
     int Q = 0, maxW = 0, n_cwarps = 1;
+    size_t max_stride = 0;
     int64_t total_cta = 0, total_panels = 0;
     // table offsets (from the workspace base)
     size_t off_cta_prefix = 0, off_panel_prefix = 0, off_dataset_of = 0, off_plans = 0,
@@ -76,6 +77,7 @@ int plan_batch(const int64_t* ns, const int32_t* ms, int32_t B, const givensbn_o
     L->n_cwarps = 1;
     for (const Plan& p : L->plans) {
         L->maxW = std::max(L->maxW, p.W);
+        L->max_stride = std::max(L->max_stride, p.leaf_stride);
         L->n_cwarps = std::max(L->n_cwarps, p.n_bwarps);
     }
     // largest first: walk CTAs x families per CTA
@@ -220,7 +222,7 @@ extern "C" int score_all_families_batched(const double* const* Xs, const int64_t
     v.out = reinterpret_cast<void* const*>(base + L.off_out);
     v.walk_args = base + L.off_args;
     if ((rc = launch_r0_batched(v, L.total_panels, stream))) return rc;
-    if ((rc = launch_roots_batched(v, L.total_cta, L.Q, L.maxW, precision, stream))) return rc;
+    if ((rc = launch_roots_batched(v, L.total_cta, L.Q, L.maxW, L.max_stride, precision, stream))) return rc;
     return launch_walk_batched(v, L.total_cta, L.Q, precision, opts->debug_coverage != 0,
                                L.n_cwarps, stream);
 }

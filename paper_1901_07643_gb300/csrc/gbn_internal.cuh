@@ -53,7 +53,7 @@ struct Plan {
     int W = 0;        // fixed variables that vary across the lanes of a warp, min(5, k)
     int lanes = 0;    // 2^W sub-walks per CTA
     int64_t n_cta = 0;  // 2^(k-W) CTAs
-    int order[32] = {}; // column order of R0: [W..k-1, 0..W-1, k..m-1]
+    int order[32] = {}; // column order of R0: [W..k-1, W-1..0, k..m-1]
     int panels = 0;
     int rows_per_panel = 0;
     int center = 1;
@@ -62,6 +62,7 @@ struct Plan {
     size_t off_status = 0, off_colsum = 0, off_mu = 0, off_gram = 0, off_r1 = 0, off_r1inv = 0;
     size_t off_r0 = 0;
     size_t off_leaves = 0;
+    size_t off_top = 0;      // the CTA roots of the sub-walk tree (nodes at depth k - W)
     size_t off_fix = 0;      // fix-up: [mask (u32) | pad | thr float[32]] then the slot list
     int fix_cap = 0;         // 0: no fix-up (FP64 walk, coverage mode or fixup_tau == 0)
     double fix_tau = 0.0;
@@ -76,6 +77,7 @@ int auto_q(int m, int precision);
 // Stages (each enqueues kernels on `stream`; return GBN_OK or GBN_ERR_CUDA).
 int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream);
 int launch_roots(const Plan& p, char* ws, cudaStream_t stream);
+size_t top_node_bytes(const Plan& p);
 int launch_walk(const Plan& p, char* ws, void* out, cudaStream_t stream);
 // Ill-conditioned families (FP32 walk): flag the variables whose smallest
 // possible RSS is tiny before the walk, recompute the listed families after it.
@@ -139,8 +141,8 @@ __device__ __forceinline__ int batch_locate(const BatchView& v, const int64_t* p
 }
 
 int launch_r0_batched(const BatchView& v, int64_t total_panels, cudaStream_t stream);
-int launch_roots_batched(const BatchView& v, int64_t total_cta, int Q, int max_w, int precision,
-                         cudaStream_t stream);
+int launch_roots_batched(const BatchView& v, int64_t total_cta, int Q, int max_w,
+                         size_t max_stride, int precision, cudaStream_t stream);
 int launch_walk_batched(const BatchView& v, int64_t total_cta, int Q, int precision, bool coverage,
                         int n_cwarps, cudaStream_t stream);
 

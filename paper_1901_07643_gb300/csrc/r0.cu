@@ -185,11 +185,13 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ gram, int p
         // right-looking Cholesky, lane l owns column l; row j of R replaces row j of G
         for (int j = 0; j < m; ++j) {
             const double d = G[j * kLd + j];
-            const double rjj = d > 0.0 ? sqrt(d) : 0.0;
+            // one reciprocal square root per column; the row is scaled by it
+            const double inv = d > 0.0 ? rsqrt(d) : 0.0;
+            const double rjj = d * inv;
             if (lane == 0 && !(d > 0.0)) atomicOr(status, GBN_STATUS_RANK_DEFICIENT);
             __syncwarp();
             if (lane >= j && lane < m)
-                G[j * kLd + lane] = (lane == j) ? rjj : (rjj != 0.0 ? G[j * kLd + lane] / rjj : 0.0);
+                G[j * kLd + lane] = (lane == j) ? rjj : G[j * kLd + lane] * inv;
             __syncwarp();
             if (lane > j && lane < m) {
                 const double rjl = G[j * kLd + lane];
@@ -197,19 +199,26 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ gram, int p
             }
             __syncwarp();
         }
-        if (!R1 && Rinv_out && lane < m) {
+        if (!R1 && Rinv_out) {
             // column `lane` of R^{-1} by back substitution (zero pivots give zero entries)
+            if (lane < m) {
+                const double rl = G[lane * kLd + lane];
+                R1s[lane] = rl != 0.0 ? 1.0 / rl : 0.0;  // reciprocal of the diagonal
+            }
+            __syncwarp();
             double x[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) x[i] = 0.0;
-            for (int i = lane; i >= 0; --i) {
-                double s = (i == lane) ? 1.0 : 0.0;
-                for (int l = i + 1; l <= lane; ++l) s -= G[i * kLd + l] * x[l];
-                const double rii = G[i * kLd + i];
-                x[i] = rii != 0.0 ? s / rii : 0.0;
-            }
-            for (int i = 0; i < m; ++i)
-                if (GBN_IN(chk, 126, i * m + lane, m * m)) Rinv_out[i * m + lane] = (i <= lane) ? x[i] : 0.0;
+            if (lane < m)
+                for (int i = lane; i >= 0; --i) {
+                    double s = (i == lane) ? 1.0 : 0.0;
+                    for (int l = i + 1; l <= lane; ++l) s -= G[i * kLd + l] * x[l];
+                    x[i] = s * R1s[i];
+                }
+            if (lane < m)
+                for (int i = 0; i < m; ++i)
+                    if (GBN_IN(chk, 126, i * m + lane, m * m))
+                        Rinv_out[i * m + lane] = (i <= lane) ? x[i] : 0.0;
         }
     }
     __syncthreads();

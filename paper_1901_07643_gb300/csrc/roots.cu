@@ -16,167 +16,251 @@
 // or joins B -- its column leaves the triangle, the remaining upper-Hessenberg
 // block is re-triangularised with one Givens rotation per row pair, the
 // deleted column is carried along (rotated with the rest) and the row that
-// falls off the bottom is added to its residual.
+// falls off the bottom is added to its residual.  Lane l owns column l of R0
+// (plan order) throughout: columns never move, a decision only changes the
+// lane's role (undecided / in F / carried in B) and drops one row.
 //
-// One warp per CTA of the walk; lane l owns column l of R0 (plan order) for
-// the whole tree and keeps it in registers: columns never move, deciding a
-// variable only changes the lane's role (undecided / in F / carried in B)
-// and drops one row.  The warp follows its CTA's path through the k - W top
-// levels, then enumerates the 2^W leaves of the last W levels depth first,
-// saving each level's node in shared memory to restart from it, and writes
-// every leaf, lane-interleaved, into the leaf record the walk reads.
+// Two kernels, each with a small instruction footprint:
+//   * top: one warp per walk CTA follows the CTA's path through the k - W top
+//     levels on a node kept in shared memory (rows addressed through a moving
+//     first-row offset, a compact loop per rotation) and stores the node it
+//     reaches: the Q + W live rows of every column, the residuals and the
+//     carried-column mask;
+//   * leaves: one warp per walk CTA loads that node into registers (at most
+//     16 rows) and enumerates the 2^W leaves of the last W levels depth first,
+//     saving each level's node in shared memory to restart from it, and
+//     writes every leaf, lane-interleaved, into the record the walk reads.
 #include <math.h>
+
+#include <utility>
 
 #include "gbn_internal.cuh"
 
 namespace gbn {
 namespace {
 
-constexpr int kMaxRows = 32;
+constexpr int kDfsRows = 16;  // register rows of the depth-first nodes (Q + W <= 16)
+constexpr int kTopWarps = 4;  // warps per block of the top kernel (one CTA root each)
+constexpr int kDfsWarps = 4;  // warps per block of the leaf kernel (one walk CTA each)
+
+// Compile-time loop: f(integral_constant<int, i>) for i in the sequence, so
+// that register arrays are only ever indexed by constants.
+template <int... Is, typename F>
+__device__ __forceinline__ void sfor(std::integer_sequence<int, Is...>, F&& f) {
+    (f(std::integral_constant<int, Is>{}), ...);
+}
 
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
-// Include: the front variable joins F.  Drop row 0 (all lanes shift their rows).
 template <typename T>
-__device__ __forceinline__ void drop_first_row(T (&M)[kMaxRows]) {
-#pragma unroll
-    for (int r = 0; r + 1 < kMaxRows; ++r) M[r] = M[r + 1];
-    M[kMaxRows - 1] = T(0);
+__device__ __forceinline__ void givens_cs(T a, T b, T& c, T& s) {
+    const T r2 = fma(a, a, b * b);  // explicit fma: every instance rounds alike
+    c = T(1);
+    s = T(0);
+    if (r2 > T(0)) {
+        const T inv = rsqrt_t(r2);
+        c = a * inv;
+        s = b * inv;
+    }
 }
 
-// Exclude: the column at lane `front` leaves the triangle (it is carried from
-// now on); rows 0 .. p-1 of the live columns front+1 .. front+p-1 are
+// Size of a stored node with `rows` rows: the rows, the residuals, the
+// carried mask (one element of T, read as a word), all lane-interleaved.
+__host__ __device__ __forceinline__ size_t node_elems(int rows) { return (size_t)(rows + 2) * 32; }
+
+template <typename T>
+__device__ __forceinline__ unsigned* mask_of(T* node, int rows) {
+    return reinterpret_cast<unsigned*>(node + (size_t)(rows + 1) * 32);
+}
+
+// The variable of R0 column (lane) `lane`: the plan order is
+// [W..k-1, W-1..0, free variables].
+__device__ __forceinline__ int var_of_lane(const Plan& p, int lane) {
+    const int kw = p.k - p.W;
+    return lane < kw ? lane + p.W : (lane < p.k ? p.W - 1 - (lane - kw) : lane);
+}
+
+// ------------------------------------------------------------- top levels
+
+template <typename T>
+__device__ __forceinline__ void top_body(const double* __restrict__ R0, const Plan& p,
+                                         T* __restrict__ top, unsigned long long* chk,
+                                         uint64_t cta, T* S /* 32 x 32, [row * 32 + lane] */) {
+    const int lane = threadIdx.x & 31, m = p.m;
+    for (int r = 0; r < 32; ++r)
+        S[r * 32 + lane] = (r < m && lane < m && GBN_IN(chk, 231, r * m + lane, m * m))
+                               ? (T)R0[r * m + lane]
+                               : T(0);
+    __syncwarp();
+    T C = T(0);
+    unsigned carried = 0u;
+    int r0 = 0, rows = m;  // live rows r0 .. r0 + rows - 1
+    for (int f = 0; f < p.k - p.W; ++f) {
+        if ((cta >> f) & 1ull) {  // include: the first live row goes
+            ++r0;
+            --rows;
+            continue;
+        }
+        carried |= 1u << f;  // exclude: column f leaves the triangle
+        for (int j = 0; j + 1 < rows; ++j) {
+            const int ra = r0 + j, piv = f + 1 + j;
+            const T a = S[ra * 32 + piv], b = S[(ra + 1) * 32 + piv];
+            const T x = S[ra * 32 + lane], y = S[(ra + 1) * 32 + lane];
+            T c, s;
+            givens_cs(a, b, c, s);
+            __syncwarp();
+            S[ra * 32 + lane] = fma(c, x, s * y);
+            S[(ra + 1) * 32 + lane] = fma(c, y, -s * x);
+            __syncwarp();
+        }
+        const T yb = S[(r0 + rows - 1) * 32 + lane];  // the bottom row falls off
+        if ((carried >> lane) & 1u) C = fma(yb, yb, C);
+        --rows;
+    }
+    // rows == Q + W: store the node
+    T* out = top + (size_t)cta * node_elems(rows);
+    for (int r = 0; r < rows; ++r) out[(size_t)r * 32 + lane] = S[(r0 + r) * 32 + lane];
+    out[(size_t)rows * 32 + lane] = C;
+    if (lane == 0) *mask_of(out, rows) = carried;
+}
+
+// ------------------------------------------------------------- last W levels
+
+// Include: the front variable joins F.  Drop row 0 (all lanes shift their rows).
+template <typename T>
+__device__ __forceinline__ void drop_first_row(T (&M)[kDfsRows]) {
+    sfor(std::make_integer_sequence<int, kDfsRows - 1>{}, [&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        M[r] = M[r + 1];
+    });
+    M[kDfsRows - 1] = T(0);
+}
+
+// Exclude: the column at lane `front` leaves the triangle (carried from now
+// on); rows 0 .. p-1 of the live columns front+1 .. front+p-1 are
 // re-triangularised, every lane applying the same rotations to its column;
 // carried lanes add the dropped bottom row p-1 to their residual.
 template <typename T>
-__device__ __forceinline__ void exclude_front(T (&M)[kMaxRows], T& C, int lane, int front, int p,
+__device__ __forceinline__ void exclude_front(T (&M)[kDfsRows], T& C, int front, int p,
                                               bool carried) {
-#pragma unroll
-    for (int j = 0; j + 1 < kMaxRows; ++j) {
+    sfor(std::make_integer_sequence<int, kDfsRows - 1>{}, [&](auto jc) {
+        constexpr int j = decltype(jc)::value;
         if (j + 1 < p) {
             const int piv = front + 1 + j;
             const T a = __shfl_sync(0xffffffffu, M[j], piv);
             const T b = __shfl_sync(0xffffffffu, M[j + 1], piv);
-            const T r2 = a * a + b * b;
-            T c = T(1), s = T(0), rho = T(0);
-            if (r2 > T(0)) {
-                const T inv = rsqrt_t(r2);
-                c = a * inv;
-                s = b * inv;
-                rho = r2 * inv;
-            }
+            T c, s;
+            givens_cs(a, b, c, s);
             const T x = M[j], y = M[j + 1];
-            M[j] = (lane == piv) ? rho : c * x + s * y;
-            M[j + 1] = (lane == piv) ? T(0) : c * y - s * x;
+            M[j] = fma(c, x, s * y);
+            M[j + 1] = fma(c, y, -s * x);
         }
-    }
-    // the bottom row p-1 falls off: into the residual of carried columns
-#pragma unroll
-    for (int r = 0; r < kMaxRows; ++r) {
+    });
+    sfor(std::make_integer_sequence<int, kDfsRows>{}, [&](auto rc) {
+        constexpr int r = decltype(rc)::value;
         if (r == p - 1) {
             if (carried) C = fma(M[r], M[r], C);
             M[r] = T(0);
         }
-    }
+    });
 }
 
 template <typename T>
-__device__ __forceinline__ void decide(T (&M)[kMaxRows], T& C, unsigned& carried_mask, int lane,
+__device__ __forceinline__ void decide(T (&M)[kDfsRows], T& C, unsigned& carried_mask, int lane,
                                        int front, int p, bool include) {
     if (include) {
         drop_first_row(M);
     } else {
         carried_mask |= 1u << front;
-        exclude_front(M, C, lane, front, p, (carried_mask >> lane) & 1u);
+        exclude_front(M, C, front, p, (carried_mask >> lane) & 1u);
     }
 }
 
-// Save / restore the lane's rows 0 .. rows-1 and residual (shared memory,
-// [slot][row][lane], conflict-free).
-// A slot holds `rows` rows and then the residual: (rows + 1) x 32 elements.
 template <typename T>
-__device__ __forceinline__ void save_node(T* st, const T (&M)[kMaxRows], T C, int lane, int rows) {
-#pragma unroll
-    for (int r = 0; r < kMaxRows; ++r)
+__device__ __forceinline__ void save_node(T* st, const T (&M)[kDfsRows], T C, unsigned carried,
+                                          int lane, int rows) {
+    sfor(std::make_integer_sequence<int, kDfsRows>{}, [&](auto rc) {
+        constexpr int r = decltype(rc)::value;
         if (r < rows) st[r * 32 + lane] = M[r];
+    });
     st[rows * 32 + lane] = C;
-}
-template <typename T>
-__device__ __forceinline__ void load_node(const T* st, T (&M)[kMaxRows], T& C, int lane, int rows) {
-#pragma unroll
-    for (int r = 0; r < kMaxRows; ++r) M[r] = (r < rows) ? st[r * 32 + lane] : T(0);
-    C = st[rows * 32 + lane];
+    if (lane == 0) *mask_of(st, rows) = carried;
+    __syncwarp();
 }
 
-// Leaf record of sub-walk ell (lane-interleaved, see gbn_internal.cuh).
 template <typename T>
-__device__ __forceinline__ void write_leaf(const T (&M)[kMaxRows], T C, const Plan& p, int lane,
+__device__ __forceinline__ void load_node(const T* st, T (&M)[kDfsRows], T& C, unsigned& carried,
+                                          int lane, int rows) {
+    sfor(std::make_integer_sequence<int, kDfsRows>{}, [&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        M[r] = (r < rows) ? st[r * 32 + lane] : T(0);
+    });
+    C = st[rows * 32 + lane];
+    carried = *mask_of(const_cast<T*>(st), rows);
+}
+
+// Write leaf ell's record straight to the CTA's record (lane-interleaved).
+template <typename T>
+__device__ __forceinline__ void write_leaf(const T (&M)[kDfsRows], T C, const Plan& p, int lane,
                                            unsigned carried_mask, int ell, T* rec,
                                            unsigned long long* chk) {
     const int Q = p.Q, k = p.k, LQ = Q * (Q + 1) / 2;
     if (lane >= k && lane < p.m) {  // L column i: rows 0 .. i of the L block
         const int i = lane - k;
-#pragma unroll
-        for (int r = 0; r < kMaxRows; ++r) {
+        sfor(std::make_integer_sequence<int, kDfsRows>{}, [&](auto rc) {
+            constexpr int r = decltype(rc)::value;
             if (r <= i) {
                 const size_t ix = (size_t)(i * (i + 1) / 2 + r) * 32 + ell;
                 if (GBN_IN(chk, 221, ix, p.leaf_stride)) rec[ix] = M[r];
             }
-        }
+        });
     } else if (lane < k && ((carried_mask >> lane) & 1u)) {  // fixed variable in B
-        const int v = p.order[lane];
-        const size_t b0 = (size_t)(LQ + v * (Q + 1)) * 32 + ell;
-#pragma unroll
-        for (int r = 0; r < kMaxRows; ++r) {
+        const size_t b0 = (size_t)(LQ + var_of_lane(p, lane) * (Q + 1)) * 32 + ell;
+        sfor(std::make_integer_sequence<int, kDfsRows>{}, [&](auto rc) {
+            constexpr int r = decltype(rc)::value;
             if (r < Q) {
                 const size_t ix = b0 + (size_t)r * 32;
                 if (GBN_IN(chk, 224, ix, p.leaf_stride)) rec[ix] = M[r];
             }
-        }
+        });
         const size_t ix = b0 + (size_t)Q * 32;
         if (GBN_IN(chk, 225, ix, p.leaf_stride)) rec[ix] = C;
     }
 }
 
+// Shared-memory elements of one warp's depth-first stack: level t holds a
+// node of Q + W - t rows.
+__host__ __device__ __forceinline__ size_t dfs_stack_elems(int Q, int W) {
+    size_t e = 0;
+    for (int t = 0; t < W; ++t) e += node_elems(Q + W - t);
+    return e > 0 ? e : 32;
+}
+
 template <typename T>
-__device__ __forceinline__ void roots_body(const double* __restrict__ R0, const Plan& p,
-                                           T* __restrict__ leaves, unsigned long long* chk,
-                                           uint64_t cta) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* stack = reinterpret_cast<T*>(smem_raw);  // W slots of (Q + W + 1) x 32
+__device__ __forceinline__ void leaves_body(const T* __restrict__ top, const Plan& p,
+                                            T* __restrict__ leaves, unsigned long long* chk,
+                                            uint64_t cta, T* stack) {
     const int lane = threadIdx.x & 31;
-    const int m = p.m;
-    T M[kMaxRows];
-#pragma unroll
-    for (int r = 0; r < kMaxRows; ++r)
-        M[r] = (r < m && lane < m && GBN_IN(chk, 231, r * m + lane, m * m)) ? (T)R0[r * m + lane]
-                                                                         : T(0);
-    T C = T(0);
-    unsigned carried = 0u;
-    int front = 0;
-    for (; front < p.k - p.W; ++front)
-        decide(M, C, carried, lane, front, m - front, ((cta >> front) & 1ull) != 0ull);
+    const int W = p.W, rows_top = p.Q + W, topk = p.k - W;
+    T M[kDfsRows];
+    T C;
+    unsigned carried;
+    load_node(top + (size_t)cta * node_elems(rows_top), M, C, carried, lane, rows_top);
     T* rec = leaves + (size_t)cta * p.leaf_stride;
-    const int top = front;
-    const unsigned carried_top = carried;
-    const size_t slot = (size_t)(p.Q + p.W + 1) * 32;  // rows at level t: Q + W - t
-    unsigned carried_at[8];
     int prev = 0;
-    for (int lam = 0; lam < p.lanes; ++lam) {
-        const int ell = (p.W > 0) ? (int)(__brev((unsigned)lam) >> (32 - p.W)) : 0;
-        const int t0 = (lam == 0) ? 0 : __ffs(ell ^ prev) - 1;
-        if (lam > 0) {
-            load_node(stack + (size_t)t0 * slot, M, C, lane, m - top - t0);
-            carried = carried_at[t0];
-        } else {
-            carried = carried_top;
-        }
-        for (int t = t0; t < p.W; ++t) {
-            const int rows = m - top - t;
-            save_node(stack + (size_t)t * slot, M, C, lane, rows);
-            carried_at[t] = carried;
-            decide(M, C, carried, lane, top + t, rows, ((ell >> t) & 1) != 0);
+    for (int ell = 0; ell < p.lanes; ++ell) {
+        // level t decides the fixed variable W-1-t with bit W-1-t of ell, so
+        // consecutive leaves differ in the deepest levels first
+        const int t0 = (ell == 0) ? 0 : W - 1 - (31 - __clz(ell ^ prev));
+        size_t off = 0;
+        for (int t = 0; t < t0; ++t) off += node_elems(rows_top - t);
+        if (ell > 0) load_node(stack + off, M, C, carried, lane, rows_top - t0);
+        for (int t = t0; t < W; ++t) {
+            const int rows = rows_top - t;
+            save_node(stack + off, M, C, carried, lane, rows);
+            off += node_elems(rows);
+            decide(M, C, carried, lane, topk + t, rows, ((ell >> (W - 1 - t)) & 1) != 0);
         }
         write_leaf(M, C, p, lane, carried, ell, rec, chk);
         prev = ell;
@@ -184,69 +268,116 @@ __device__ __forceinline__ void roots_body(const double* __restrict__ R0, const 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32) roots_kernel(const Plan p, char* ws) {
-    roots_body<T>(reinterpret_cast<const double*>(ws + p.off_r0), p,
-                  reinterpret_cast<T*>(ws + p.off_leaves),
-                  reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset),
-                  blockIdx.x);
+__device__ __forceinline__ T* top_nodes(const Plan& p, char* ws) {
+    return reinterpret_cast<T*>(ws + p.off_top);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32) roots_kernel_b(const BatchView v) {
+__global__ void __launch_bounds__(32 * kTopWarps) roots_top_kernel(const Plan p, char* ws) {
+    __shared__ T S[kTopWarps * 32 * 32];
+    const int warp = threadIdx.x >> 5;
+    const uint64_t cta = (uint64_t)blockIdx.x * kTopWarps + warp;
+    if (cta >= (uint64_t)p.n_cta) return;
+    top_body<T>(reinterpret_cast<const double*>(ws + p.off_r0), p, top_nodes<T>(p, ws),
+                reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset), cta,
+                S + warp * 32 * 32);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kDfsWarps) roots_leaves_kernel(const Plan p, char* ws) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    const uint64_t cta = (uint64_t)blockIdx.x * kDfsWarps + warp;
+    if (cta >= (uint64_t)p.n_cta) return;
+    T* stack = reinterpret_cast<T*>(smem_raw) + warp * dfs_stack_elems(p.Q, p.W);
+    leaves_body<T>(top_nodes<T>(p, ws), p, reinterpret_cast<T*>(ws + p.off_leaves),
+                   reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset), cta,
+                   stack);
+}
+
+// A batch: warps find their dataset through the prefix of walk CTAs.
+template <typename T>
+__global__ void __launch_bounds__(32 * kTopWarps) roots_top_kernel_b(const BatchView v) {
+    __shared__ T S[kTopWarps * 32 * 32];
+    const int warp = threadIdx.x >> 5;
+    const int64_t g = (int64_t)blockIdx.x * kTopWarps + warp;
+    if (g >= v.cta_prefix[v.B]) return;
     int64_t local;
-    const int d = batch_locate(v, v.cta_prefix, blockIdx.x, local);
+    const int d = batch_locate(v, v.cta_prefix, g, local);
     const Plan& p = v.plans[d];
     char* ws = v.ws[d];
-    roots_body<T>(reinterpret_cast<const double*>(ws + p.off_r0), p,
-                  reinterpret_cast<T*>(ws + p.off_leaves),
-                  reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset),
-                  (uint64_t)local);
+    top_body<T>(reinterpret_cast<const double*>(ws + p.off_r0), p, top_nodes<T>(p, ws),
+                reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset),
+                (uint64_t)local, S + warp * 32 * 32);
 }
 
 template <typename T>
-size_t roots_smem(int Q, int W) {
-    return sizeof(T) * (size_t)(Q + W + 1) * 32 * (size_t)(W > 0 ? W : 1);
+__global__ void __launch_bounds__(32 * kDfsWarps) roots_leaves_kernel_b(const BatchView v,
+                                                                         int Q, int max_w) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    const int64_t g = (int64_t)blockIdx.x * kDfsWarps + warp;
+    if (g >= v.cta_prefix[v.B]) return;
+    int64_t local;
+    const int d = batch_locate(v, v.cta_prefix, g, local);
+    const Plan& p = v.plans[d];
+    char* ws = v.ws[d];
+    T* stack = reinterpret_cast<T*>(smem_raw) + warp * dfs_stack_elems(Q, max_w);
+    leaves_body<T>(top_nodes<T>(p, ws), p, reinterpret_cast<T*>(ws + p.off_leaves),
+                   reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset),
+                   (uint64_t)local, stack);
 }
 
 template <typename T>
-int set_roots_smem() {
-    static bool attr_set = false;  // per process; every device gets the same attribute value
-    if (!attr_set) {
-        const int bytes = (int)roots_smem<T>(kMaxRows, kLaneBits);
-        if (cudaFuncSetAttribute(roots_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 bytes) != cudaSuccess ||
-            cudaFuncSetAttribute(roots_kernel_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 bytes) != cudaSuccess)
-            return GBN_ERR_CUDA;
-        attr_set = true;
-    }
+int roots_attr(size_t smem) {
+    if (cudaFuncSetAttribute(roots_leaves_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(roots_leaves_kernel_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return GBN_ERR_CUDA;
     return GBN_OK;
 }
 
 template <typename T>
 int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
-    if (set_roots_smem<T>()) return GBN_ERR_CUDA;
-    roots_kernel<T><<<(unsigned)p.n_cta, 32, roots_smem<T>(p.Q, p.W), stream>>>(p, ws);
+    if (p.Q + p.W > kDfsRows) return GBN_ERR_Q;
+    const size_t smem = sizeof(T) * dfs_stack_elems(p.Q, p.W) * kDfsWarps;
+    if (roots_attr<T>(smem)) return GBN_ERR_CUDA;
+    const unsigned nb_top = (unsigned)((p.n_cta + kTopWarps - 1) / kTopWarps);
+    const unsigned nb_dfs = (unsigned)((p.n_cta + kDfsWarps - 1) / kDfsWarps);
+    roots_top_kernel<T><<<nb_top, 32 * kTopWarps, 0, stream>>>(p, ws);
+    roots_leaves_kernel<T><<<nb_dfs, 32 * kDfsWarps, smem, stream>>>(p, ws);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
 template <typename T>
 int launch_roots_batched_t(const BatchView& v, int64_t total_cta, int Q, int max_w,
                            cudaStream_t stream) {
-    if (set_roots_smem<T>()) return GBN_ERR_CUDA;
-    roots_kernel_b<T><<<(unsigned)total_cta, 32, roots_smem<T>(Q, max_w), stream>>>(v);
+    if (Q + max_w > kDfsRows) return GBN_ERR_Q;
+    const size_t smem = sizeof(T) * dfs_stack_elems(Q, max_w) * kDfsWarps;
+    if (roots_attr<T>(smem)) return GBN_ERR_CUDA;
+    const unsigned nb_top = (unsigned)((total_cta + kTopWarps - 1) / kTopWarps);
+    const unsigned nb_dfs = (unsigned)((total_cta + kDfsWarps - 1) / kDfsWarps);
+    roots_top_kernel_b<T><<<nb_top, 32 * kTopWarps, 0, stream>>>(v);
+    roots_leaves_kernel_b<T><<<nb_dfs, 32 * kDfsWarps, smem, stream>>>(v, Q, max_w);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
 }  // namespace
+
+size_t top_node_bytes(const Plan& p) {
+    const size_t es = p.precision ? sizeof(double) : sizeof(float);
+    return es * node_elems(p.Q + p.W) * (size_t)p.n_cta;
+}
 
 int launch_roots(const Plan& p, char* ws, cudaStream_t stream) {
     return p.precision ? launch_roots_t<double>(p, ws, stream)
                        : launch_roots_t<float>(p, ws, stream);
 }
 
-int launch_roots_batched(const BatchView& v, int64_t total_cta, int Q, int max_w, int precision,
-                         cudaStream_t stream) {
+int launch_roots_batched(const BatchView& v, int64_t total_cta, int Q, int max_w,
+                         size_t max_stride, int precision, cudaStream_t stream) {
+    (void)max_stride;
     return precision ? launch_roots_batched_t<double>(v, total_cta, Q, max_w, stream)
                      : launch_roots_batched_t<float>(v, total_cta, Q, max_w, stream);
 }
