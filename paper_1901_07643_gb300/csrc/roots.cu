@@ -267,6 +267,148 @@ __device__ __forceinline__ void leaves_body(const T* __restrict__ top, const Pla
     }
 }
 
+// ---- the depth-first part for W = 5 with Q known at compile time: every
+// level's row count is a constant, so each level's code does exactly its
+// rotations and row moves, with no guards.
+template <int RT, int L>
+constexpr size_t stack_off() {
+    size_t e = 0;
+    for (int u = 0; u < L; ++u) e += (size_t)(RT - u + 2) * 32;
+    return e;
+}
+
+template <typename T, int RT, int rows>
+__device__ __forceinline__ void exclude_n(T (&M)[RT], T& C, int front, bool carried) {
+    sfor(std::make_integer_sequence<int, rows - 1>{}, [&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        const int piv = front + 1 + j;
+        const T a = __shfl_sync(0xffffffffu, M[j], piv);
+        const T b = __shfl_sync(0xffffffffu, M[j + 1], piv);
+        T c, s;
+        givens_cs(a, b, c, s);
+        const T x = M[j], y = M[j + 1];
+        M[j] = fma(c, x, s * y);
+        M[j + 1] = fma(c, y, -s * x);
+    });
+    if (carried) C = fma(M[rows - 1], M[rows - 1], C);
+    M[rows - 1] = T(0);
+}
+
+template <typename T, int RT, int rows>
+__device__ __forceinline__ void include_n(T (&M)[RT]) {
+    sfor(std::make_integer_sequence<int, rows - 1>{}, [&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        M[r] = M[r + 1];
+    });
+    M[rows - 1] = T(0);
+}
+
+template <typename T, int RT, int rows>
+__device__ __forceinline__ void save_n(T* st, const T (&M)[RT], T C, unsigned carried, int lane) {
+    sfor(std::make_integer_sequence<int, rows>{}, [&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        st[r * 32 + lane] = M[r];
+    });
+    st[rows * 32 + lane] = C;
+    if (lane == 0) *mask_of(st, rows) = carried;
+    __syncwarp();
+}
+
+template <typename T, int RT, int rows>
+__device__ __forceinline__ void load_n(const T* st, T (&M)[RT], T& C, unsigned& carried, int lane) {
+    sfor(std::make_integer_sequence<int, rows>{}, [&](auto rc) {
+        constexpr int r = decltype(rc)::value;
+        M[r] = st[r * 32 + lane];
+    });
+    C = st[rows * 32 + lane];
+    carried = *mask_of(const_cast<T*>(st), rows);
+}
+
+template <typename T, int Q, int RT>
+__device__ __forceinline__ void write_leaf_q(const T (&M)[RT], T C, const Plan& p, int lane,
+                                             unsigned carried_mask, int ell, T* rec,
+                                             unsigned long long* chk) {
+    constexpr int LQ = Q * (Q + 1) / 2;
+    const int k = p.k;
+    if (lane >= k && lane < p.m) {  // L column i: rows 0 .. i of the L block
+        const int i = lane - k;
+        const size_t b0 = (size_t)(i * (i + 1) / 2) * 32 + ell;
+        sfor(std::make_integer_sequence<int, Q>{}, [&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            if (r <= i && GBN_IN(chk, 221, b0 + (size_t)r * 32, p.leaf_stride))
+                rec[b0 + (size_t)r * 32] = M[r];
+        });
+    } else if (lane < k && ((carried_mask >> lane) & 1u)) {  // fixed variable in B
+        const size_t b0 = (size_t)(LQ + var_of_lane(p, lane) * (Q + 1)) * 32 + ell;
+        sfor(std::make_integer_sequence<int, Q>{}, [&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            if (GBN_IN(chk, 224, b0 + (size_t)r * 32, p.leaf_stride)) rec[b0 + (size_t)r * 32] = M[r];
+        });
+        if (GBN_IN(chk, 225, b0 + (size_t)Q * 32, p.leaf_stride)) rec[b0 + (size_t)Q * 32] = C;
+    }
+}
+
+// Level L of the depth-first enumeration: save the node, then for each
+// choice of the level's variable (join F first, then join B) build the child
+// and descend.  One copy of each level's code.
+template <typename T, int Q, int L>
+struct Dfs5 {
+    static constexpr int W = 5, RT = Q + W, rows = RT - L;
+    __device__ static __forceinline__ void run(T (&M)[RT], T& C, unsigned& carried, int lane,
+                                               int topk, int ell, T* stack, const Plan& p, T* rec,
+                                               unsigned long long* chk) {
+        if constexpr (L == W) {
+            write_leaf_q<T, Q, RT>(M, C, p, lane, carried, ell, rec, chk);
+        } else {
+            T* slot = stack + stack_off<RT, L>();
+            save_n<T, RT, rows>(slot, M, C, carried, lane);
+#pragma unroll 1
+            for (int b = 1; b >= 0; --b) {
+                if (b) {
+                    include_n<T, RT, rows>(M);
+                } else {
+                    load_n<T, RT, rows>(slot, M, C, carried, lane);
+                    carried |= 1u << (topk + L);
+                    exclude_n<T, RT, rows>(M, C, topk + L, (carried >> lane) & 1u);
+                }
+                Dfs5<T, Q, L + 1>::run(M, C, carried, lane, topk, ell | (b << (W - 1 - L)), stack,
+                                       p, rec, chk);
+            }
+        }
+    }
+};
+
+template <typename T, int Q>
+__device__ __forceinline__ void leaves_w5(const T* __restrict__ top, const Plan& p,
+                                          T* __restrict__ leaves, unsigned long long* chk,
+                                          uint64_t cta, T* stack) {
+    constexpr int RT = Q + 5;
+    const int lane = threadIdx.x & 31;
+    T M[RT];
+    T C;
+    unsigned carried;
+    load_n<T, RT, RT>(top + (size_t)cta * node_elems(RT), M, C, carried, lane);
+    Dfs5<T, Q, 0>::run(M, C, carried, lane, p.k - 5, 0, stack, p, leaves + (size_t)cta * p.leaf_stride,
+                       chk);
+}
+
+// The specialised enumeration when W = 5 and Q is one of the compiled sizes.
+template <typename T>
+__device__ __forceinline__ bool leaves_fast(const T* __restrict__ top, const Plan& p,
+                                            T* __restrict__ leaves, unsigned long long* chk,
+                                            uint64_t cta, T* stack) {
+    if (p.W != 5) return false;
+    switch (p.Q) {
+        case 4: leaves_w5<T, 4>(top, p, leaves, chk, cta, stack); return true;
+        case 5: leaves_w5<T, 5>(top, p, leaves, chk, cta, stack); return true;
+        case 6: leaves_w5<T, 6>(top, p, leaves, chk, cta, stack); return true;
+        case 7: leaves_w5<T, 7>(top, p, leaves, chk, cta, stack); return true;
+        case 8: leaves_w5<T, 8>(top, p, leaves, chk, cta, stack); return true;
+        case 9: leaves_w5<T, 9>(top, p, leaves, chk, cta, stack); return true;
+        default: return false;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T* top_nodes(const Plan& p, char* ws) {
     return reinterpret_cast<T*>(ws + p.off_top);
@@ -290,9 +432,10 @@ __global__ void __launch_bounds__(32 * kDfsWarps) roots_leaves_kernel(const Plan
     const uint64_t cta = (uint64_t)blockIdx.x * kDfsWarps + warp;
     if (cta >= (uint64_t)p.n_cta) return;
     T* stack = reinterpret_cast<T*>(smem_raw) + warp * dfs_stack_elems(p.Q, p.W);
-    leaves_body<T>(top_nodes<T>(p, ws), p, reinterpret_cast<T*>(ws + p.off_leaves),
-                   reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset), cta,
-                   stack);
+    T* leaves = reinterpret_cast<T*>(ws + p.off_leaves);
+    unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
+    if (!leaves_fast<T>(top_nodes<T>(p, ws), p, leaves, chk, cta, stack))
+        leaves_body<T>(top_nodes<T>(p, ws), p, leaves, chk, cta, stack);
 }
 
 // A batch: warps find their dataset through the prefix of walk CTAs.
@@ -323,9 +466,10 @@ __global__ void __launch_bounds__(32 * kDfsWarps) roots_leaves_kernel_b(const Ba
     const Plan& p = v.plans[d];
     char* ws = v.ws[d];
     T* stack = reinterpret_cast<T*>(smem_raw) + warp * dfs_stack_elems(Q, max_w);
-    leaves_body<T>(top_nodes<T>(p, ws), p, reinterpret_cast<T*>(ws + p.off_leaves),
-                   reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset),
-                   (uint64_t)local, stack);
+    T* leaves = reinterpret_cast<T*>(ws + p.off_leaves);
+    unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
+    if (!leaves_fast<T>(top_nodes<T>(p, ws), p, leaves, chk, (uint64_t)local, stack))
+        leaves_body<T>(top_nodes<T>(p, ws), p, leaves, chk, (uint64_t)local, stack);
 }
 
 template <typename T>
