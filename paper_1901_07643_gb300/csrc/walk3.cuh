@@ -101,6 +101,7 @@ inline WalkArgs<T> make_walk_args(const Plan& p, char* ws, void* out) {
 }
 
 constexpr int kChunk = 16;  // tape steps per barrier
+constexpr int kHalfMinQ = 5;  // from this Q on, the consumers replay one code copy per half
 
 // The swap sequence of Algorithm 1 with, per step, the 0-based swap row i
 // (the paper's GRC_{i+1}) and the mask of the local free variables at
@@ -144,6 +145,12 @@ constexpr StepTab<Q> make_step_tab() {
 
 template <int Q>
 inline constexpr StepTab<Q> kSteps = make_step_tab<Q>();
+
+#ifdef GBN_Q
+// The step table of this translation unit's Q in constant memory (the
+// producer's rows, the consumers' run-time prefix masks).
+__constant__ StepTab<GBN_Q> c_steps = make_step_tab<GBN_Q>();
+#endif
 
 __device__ __forceinline__ float wk_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double wk_rsqrt(double x) { return rsqrt(x); }
@@ -425,6 +432,115 @@ __device__ __forceinline__ bool replay(const WalkArgs<T>& a, const typename Vec2
     return ok;
 }
 
+#ifdef GBN_Q
+// The same replay with half the code, using the recursion of Algorithm 1:
+// Upsilon(Q) = Upsilon(Q-1) : [Q-1 .. 1] : (Upsilon(Q-1) + 1).  One copy of
+// the Upsilon(Q-1) steps runs twice -- first on rows 0 .. Q-2, then, after
+// the chain that moves the last free variable to the front, on rows 1 .. Q-1
+// through a one-row shifted view of the column -- with the prefix masks read
+// from the constant step table at run time.  The instruction footprint of the
+// walk is what bounds it, so halving the unrolled code pays for the extra
+// table load per step.
+template <typename T, int Q, bool COV>
+__device__ __forceinline__ bool replay_half(const WalkArgs<T>& a,
+                                            const typename Vec2T<T>::type* tape, uint64_t* full,
+                                            T (&z)[Q], T cres, int ell, int jj, int sh,
+                                            OutT<T, COV>* base, T penb, bool on) {
+    static_assert(Q == GBN_Q, "the step table in constant memory is this unit's");
+    constexpr int N = StepTab<Q>::N;
+    constexpr int Q1 = Q - 1;
+    constexpr int N1 = StepTab<Q1>::N;  // steps of each half
+    constexpr int NC = Q - 1;           // steps of the chain between the halves
+    T w[Q + 1];
+    w[Q] = cres;
+#pragma unroll
+    for (int r = Q - 1; r >= 0; --r) w[r] = fma(z[r], z[r], w[r + 1]);
+    const unsigned lm = (1u << jj) - 1u;
+    static_for(std::make_integer_sequence<int, Q + 1>{}, [&](auto sc) {  // the root's families
+        constexpr int s = decltype(sc)::value;
+        constexpr unsigned pre = (1u << s) - 1u;
+        const bool child = !((pre >> jj) & 1u);
+        const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
+        emit_ptr<T, COV>(a, base, cT << sh, w[s], fma(T(s), a.lnn, penb), on && child);
+    });
+    bool ok = true;
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        T zv[Q1], wv[Q1 + 1];  // the view: rows h .. h + Q - 2
+        if (h == 0) {
+            static_for(std::make_integer_sequence<int, Q1>{}, [&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                zv[r] = z[r];
+                wv[r] = w[r];
+            });
+            wv[Q1] = w[Q1];
+        } else {
+            static_for(std::make_integer_sequence<int, Q1>{}, [&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                zv[r] = z[r + 1];
+                wv[r] = w[r + 1];
+            });
+            wv[Q1] = w[Q];
+        }
+        const int toff = h ? N1 + NC : 0;
+        const T penh = h ? penb + a.lnn : penb;  // the moved variable is a parent throughout
+        const auto* tp = tape + (size_t)toff * 32 + ell;
+        static_for(std::make_integer_sequence<int, N1>{}, [&](auto tc) {
+            constexpr int t = decltype(tc)::value;
+            if constexpr (t % kChunk == 0) {
+                int c = (t + toff + kChunk - 1) / kChunk;
+                if (c > (N - 1) / kChunk) c = (N - 1) / kChunk;
+                if (ok) ok = warp_wait(&full[c], 0, a.watchdog_ns, a.status);
+            }
+            constexpr int i = kSteps<Q1>.row[t];
+            const unsigned pre = c_steps.pre[t + toff];
+            const auto cs = tp[t * 32];
+            const T x = zv[i], y = zv[i + 1];
+            zv[i] = fma(cs.x, x, cs.y * y);
+            const T yn = fma(cs.x, y, -cs.y * x);
+            zv[i + 1] = yn;
+            const T wn = fma(yn, yn, wv[i + 2]);
+            wv[i + 1] = wn;
+            const bool child = !((pre >> jj) & 1u);
+            const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
+            emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, penh), on && child && ok);
+        });
+        if (h == 0) {
+            static_for(std::make_integer_sequence<int, Q1>{}, [&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                z[r] = zv[r];
+                w[r] = wv[r];
+            });
+            // the chain [Q-1 .. 1]: the last free variable moves to the front
+            static_for(std::make_integer_sequence<int, NC>{}, [&](auto uc) {
+                constexpr int u = decltype(uc)::value;
+                constexpr int t = N1 + u;
+                if constexpr (t % kChunk == 0 || u == 0) {
+                    if (ok) ok = warp_wait(&full[(t + kChunk - 1) / kChunk > (N - 1) / kChunk
+                                                     ? (N - 1) / kChunk
+                                                     : (t + kChunk - 1) / kChunk],
+                                           0, a.watchdog_ns, a.status);
+                }
+                constexpr int i = kSteps<Q>.row[t];
+                constexpr unsigned pre = kSteps<Q>.pre[t];
+                const auto cs = tape[t * 32 + ell];
+                const T x = z[i], y = z[i + 1];
+                z[i] = fma(cs.x, x, cs.y * y);
+                const T yn = fma(cs.x, y, -cs.y * x);
+                z[i + 1] = yn;
+                const T wn = fma(yn, yn, w[i + 2]);
+                w[i + 1] = wn;
+                const bool child = !((pre >> jj) & 1u);
+                const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
+                emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, penb),
+                                 on && child && ok);
+            });
+        }
+    }
+    return ok;
+}
+#endif
+
 // Consumers: the CTA's columns, item it -> warp (it mod n_cwarps).
 //   items [0, Q)             free variable j = it, every lane;
 //   items [Q, Q + nu)        the fixed variables above the lowest W outside F_hi;
@@ -494,7 +610,14 @@ __device__ __forceinline__ void consume(const WalkArgs<T>& a, const T* __restric
                    (size_t)((F & lowmask) | ((F >> (v + 1)) << v));
         }
         const T penb = fma(T(__popcll(Fhi | (uint64_t)ell)), a.lnn, -a.nlnn);
-        if (!replay<T, Q, COV>(a, tape, full, z, cres, ell, jj, sh, base, penb, on)) return;
+        bool ok;
+#ifdef GBN_Q
+        if constexpr (Q >= kHalfMinQ)
+            ok = replay_half<T, Q, COV>(a, tape, full, z, cres, ell, jj, sh, base, penb, on);
+        else
+#endif
+            ok = replay<T, Q, COV>(a, tape, full, z, cres, ell, jj, sh, base, penb, on);
+        if (!ok) return;
     }
     GBN_TIMER_FLUSH(a.timing, 1)
 }
@@ -505,8 +628,6 @@ __device__ __forceinline__ void consume(const WalkArgs<T>& a, const T* __restric
 // (walk_inst.cu with -DGBN_Q=...).
 #ifdef GBN_Q
 namespace gbn {
-
-__constant__ StepTab<GBN_Q> c_steps = make_step_tab<GBN_Q>();
 
 constexpr int kMaxConsumerWarps = 8;
 
