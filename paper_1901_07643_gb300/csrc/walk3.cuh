@@ -101,7 +101,10 @@ inline WalkArgs<T> make_walk_args(const Plan& p, char* ws, void* out) {
 }
 
 constexpr int kChunk = 16;  // tape steps per barrier
-constexpr int kHalfMinQ = 5;  // from this Q on, the consumers replay one code copy per half
+// Levels of code sharing in the consumers' replay: blocks of at most
+// kSplitBase variables (|Upsilon(kSplitBase)| steps of unrolled code).
+constexpr int kSplitBase = 6;
+constexpr int split_levels(int Q) { return Q <= kSplitBase ? 0 : Q - kSplitBase; }
 
 // The swap sequence of Algorithm 1 with, per step, the 0-based swap row i
 // (the paper's GRC_{i+1}) and the mask of the local free variables at
@@ -433,24 +436,59 @@ __device__ __forceinline__ bool replay(const WalkArgs<T>& a, const typename Vec2
 }
 
 #ifdef GBN_Q
-// The same replay with half the code, using the recursion of Algorithm 1:
-// Upsilon(Q) = Upsilon(Q-1) : [Q-1 .. 1] : (Upsilon(Q-1) + 1).  One copy of
-// the Upsilon(Q-1) steps runs twice -- first on rows 0 .. Q-2, then, after
-// the chain that moves the last free variable to the front, on rows 1 .. Q-1
-// through a one-row shifted view of the column -- with the prefix masks read
-// from the constant step table at run time.  The instruction footprint of the
-// walk is what bounds it, so halving the unrolled code pays for the extra
-// table load per step.
-template <typename T, int Q, bool COV>
-__device__ __forceinline__ bool replay_half(const WalkArgs<T>& a,
-                                            const typename Vec2T<T>::type* tape, uint64_t* full,
-                                            T (&z)[Q], T cres, int ell, int jj, int sh,
-                                            OutT<T, COV>* base, T penb, bool on) {
+// The same replay with 2^-H of the code, using the recursion of Algorithm 1,
+// Upsilon(q) = Upsilon(q-1) : [q-1 .. 1] : (Upsilon(q-1) + 1), H times:
+// Upsilon(Q) is 2^H blocks of Upsilon(Q-H), block b acting on rows shifted
+// by popcount(b), each followed (except the last) by the chain of level L =
+// trailing ones of b -- [Q-H+L .. 1] shifted by popcount(b >> (L+1)).  One
+// unrolled copy of the block's steps runs 2^H times through a shifted
+// register view; each (chain length, shift) pair has one unrolled copy; the
+// prefix masks come from the constant step table at run time.  The walk is
+// bound by instruction fetch, so shrinking its code pays for the table load.
+template <int Q1, int NB>
+struct ViewCopy {  // zv/wv <-> z/w rows o .. o + Q1 (o a run-time shift 0 .. NB)
+    template <typename T, int Q>
+    __device__ static __forceinline__ void in(T (&zv)[Q1], T (&wv)[Q1 + 1], const T (&z)[Q],
+                                              const T (&w)[Q + 1], int o) {
+        static_for(std::make_integer_sequence<int, NB + 1>{}, [&](auto oc) {
+            constexpr int oo = decltype(oc)::value;
+            if (o == oo) {
+                static_for(std::make_integer_sequence<int, Q1>{}, [&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    zv[r] = z[r + oo];
+                    wv[r] = w[r + oo];
+                });
+                wv[Q1] = w[Q1 + oo];
+            }
+        });
+    }
+    template <typename T, int Q>
+    __device__ static __forceinline__ void out(const T (&zv)[Q1], const T (&wv)[Q1 + 1], T (&z)[Q],
+                                               T (&w)[Q + 1], int o) {
+        static_for(std::make_integer_sequence<int, NB + 1>{}, [&](auto oc) {
+            constexpr int oo = decltype(oc)::value;
+            if (o == oo) {
+                static_for(std::make_integer_sequence<int, Q1>{}, [&](auto rc) {
+                    constexpr int r = decltype(rc)::value;
+                    z[r + oo] = zv[r];
+                    w[r + oo] = wv[r];
+                });
+            }
+        });
+    }
+};
+
+template <typename T, int Q, int H, bool COV>
+__device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
+                                             const typename Vec2T<T>::type* tape, uint64_t* full,
+                                             T (&z)[Q], T cres, int ell, int jj, int sh,
+                                             OutT<T, COV>* base, T penb, bool on) {
     static_assert(Q == GBN_Q, "the step table in constant memory is this unit's");
+    static_assert(H >= 1 && Q - H >= 2, "blocks of at least two variables");
     constexpr int N = StepTab<Q>::N;
-    constexpr int Q1 = Q - 1;
-    constexpr int N1 = StepTab<Q1>::N;  // steps of each half
-    constexpr int NC = Q - 1;           // steps of the chain between the halves
+    constexpr int last_chunk = (N - 1) / kChunk;
+    constexpr int QB = Q - H;              // variables of a block
+    constexpr int NBLK = StepTab<QB>::N;   // steps of a block
     T w[Q + 1];
     w[Q] = cres;
 #pragma unroll
@@ -463,79 +501,65 @@ __device__ __forceinline__ bool replay_half(const WalkArgs<T>& a,
         const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
         emit_ptr<T, COV>(a, base, cT << sh, w[s], fma(T(s), a.lnn, penb), on && child);
     });
+    // one step at row i (absolute), tape step t; the mask from the table
+    auto step = [&](auto& zz, auto& ww, int i_local, auto ic, int t, T pen_base, bool& ok) {
+        constexpr int i = decltype(ic)::value;
+        (void)i_local;
+        const unsigned pre = c_steps.pre[t];
+        const auto cs = tape[(size_t)t * 32 + ell];
+        const T x = zz[i], y = zz[i + 1];
+        zz[i] = fma(cs.x, x, cs.y * y);
+        const T yn = fma(cs.x, y, -cs.y * x);
+        zz[i + 1] = yn;
+        const T wn = fma(yn, yn, ww[i + 2]);
+        ww[i + 1] = wn;
+        const bool child = !((pre >> jj) & 1u);
+        const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
+        emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, pen_base), on && child && ok);
+    };
+    auto wait_for = [&](int t, bool& ok) {  // tape steps t .. t + kChunk - 1 are written
+        int c = (t + kChunk - 1) / kChunk;
+        if (c > last_chunk) c = last_chunk;
+        if (ok) ok = warp_wait(&full[c], 0, a.watchdog_ns, a.status);
+    };
     bool ok = true;
+    int t0 = 0;  // tape step of the current block's first step
 #pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-        T zv[Q1], wv[Q1 + 1];  // the view: rows h .. h + Q - 2
-        if (h == 0) {
-            static_for(std::make_integer_sequence<int, Q1>{}, [&](auto rc) {
-                constexpr int r = decltype(rc)::value;
-                zv[r] = z[r];
-                wv[r] = w[r];
-            });
-            wv[Q1] = w[Q1];
-        } else {
-            static_for(std::make_integer_sequence<int, Q1>{}, [&](auto rc) {
-                constexpr int r = decltype(rc)::value;
-                zv[r] = z[r + 1];
-                wv[r] = w[r + 1];
-            });
-            wv[Q1] = w[Q];
-        }
-        const int toff = h ? N1 + NC : 0;
-        const T penh = h ? penb + a.lnn : penb;  // the moved variable is a parent throughout
-        const auto* tp = tape + (size_t)toff * 32 + ell;
-        static_for(std::make_integer_sequence<int, N1>{}, [&](auto tc) {
+    for (int b = 0; b < (1 << H); ++b) {
+        const int o = __popc(b);  // row shift of this block
+        T zv[QB], wv[QB + 1];
+        ViewCopy<QB, H>::template in<T, Q>(zv, wv, z, w, o);
+        const T penv = fma(T(o), a.lnn, penb);  // the o moved variables are parents throughout
+        static_for(std::make_integer_sequence<int, NBLK>{}, [&](auto tc) {
             constexpr int t = decltype(tc)::value;
-            if constexpr (t % kChunk == 0) {
-                int c = (t + toff + kChunk - 1) / kChunk;
-                if (c > (N - 1) / kChunk) c = (N - 1) / kChunk;
-                if (ok) ok = warp_wait(&full[c], 0, a.watchdog_ns, a.status);
-            }
-            constexpr int i = kSteps<Q1>.row[t];
-            const unsigned pre = c_steps.pre[t + toff];
-            const auto cs = tp[t * 32];
-            const T x = zv[i], y = zv[i + 1];
-            zv[i] = fma(cs.x, x, cs.y * y);
-            const T yn = fma(cs.x, y, -cs.y * x);
-            zv[i + 1] = yn;
-            const T wn = fma(yn, yn, wv[i + 2]);
-            wv[i + 1] = wn;
-            const bool child = !((pre >> jj) & 1u);
-            const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
-            emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, penh), on && child && ok);
+            if constexpr (t % kChunk == 0) wait_for(t0 + t, ok);
+            step(zv, wv, 0, std::integral_constant<int, kSteps<QB>.row[t]>{}, t0 + t, penv, ok);
         });
-        if (h == 0) {
-            static_for(std::make_integer_sequence<int, Q1>{}, [&](auto rc) {
-                constexpr int r = decltype(rc)::value;
-                z[r] = zv[r];
-                w[r] = wv[r];
-            });
-            // the chain [Q-1 .. 1]: the last free variable moves to the front
-            static_for(std::make_integer_sequence<int, NC>{}, [&](auto uc) {
-                constexpr int u = decltype(uc)::value;
-                constexpr int t = N1 + u;
-                if constexpr (t % kChunk == 0 || u == 0) {
-                    if (ok) ok = warp_wait(&full[(t + kChunk - 1) / kChunk > (N - 1) / kChunk
-                                                     ? (N - 1) / kChunk
-                                                     : (t + kChunk - 1) / kChunk],
-                                           0, a.watchdog_ns, a.status);
-                }
-                constexpr int i = kSteps<Q>.row[t];
-                constexpr unsigned pre = kSteps<Q>.pre[t];
-                const auto cs = tape[t * 32 + ell];
-                const T x = z[i], y = z[i + 1];
-                z[i] = fma(cs.x, x, cs.y * y);
-                const T yn = fma(cs.x, y, -cs.y * x);
-                z[i + 1] = yn;
-                const T wn = fma(yn, yn, w[i + 2]);
-                w[i + 1] = wn;
-                const bool child = !((pre >> jj) & 1u);
-                const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
-                emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, penb),
-                                 on && child && ok);
-            });
-        }
+        ViewCopy<QB, H>::template out<T, Q>(zv, wv, z, w, o);
+        t0 += NBLK;
+        if (b + 1 == (1 << H)) break;
+        // the chain after block b: level L = trailing ones of b, variables QB + 1 + L,
+        // rows shifted by popcount(b >> (L + 1))
+        const int L = __ffs(~b) - 1;
+        const int oc = __popc(b >> (L + 1));
+        wait_for(t0, ok);
+        static_for(std::make_integer_sequence<int, H>{}, [&](auto lc) {
+            constexpr int LL = decltype(lc)::value;
+            constexpr int len = QB + LL;  // chain [QB+LL .. 1]
+            if (L == LL) {
+                static_for(std::make_integer_sequence<int, H - LL>{}, [&](auto occ) {
+                    constexpr int OO = decltype(occ)::value;
+                    if (oc == OO) {
+                        static_for(std::make_integer_sequence<int, len>{}, [&](auto uc) {
+                            constexpr int u = decltype(uc)::value;
+                            constexpr int i = OO + len - 1 - u;  // absolute swap row
+                            step(z, w, 0, std::integral_constant<int, i>{}, t0 + u, penb, ok);
+                        });
+                    }
+                });
+                t0 += len;
+            }
+        });
     }
     return ok;
 }
@@ -612,8 +636,9 @@ __device__ __forceinline__ void consume(const WalkArgs<T>& a, const T* __restric
         const T penb = fma(T(__popcll(Fhi | (uint64_t)ell)), a.lnn, -a.nlnn);
         bool ok;
 #ifdef GBN_Q
-        if constexpr (Q >= kHalfMinQ)
-            ok = replay_half<T, Q, COV>(a, tape, full, z, cres, ell, jj, sh, base, penb, on);
+        if constexpr (split_levels(Q) > 0)
+            ok = replay_split<T, Q, split_levels(Q), COV>(a, tape, full, z, cres, ell, jj, sh, base,
+                                                        penb, on);
         else
 #endif
             ok = replay<T, Q, COV>(a, tape, full, z, cres, ell, jj, sh, base, penb, on);

@@ -160,3 +160,28 @@ def test_consecutive_swaps_are_adjacent(m):
     sw = seq.greedy_swaps(m)
     assert sw[0] == 1 and sw[-1] == m - 1
     assert all(abs(a - b) == 1 for a, b in zip(sw, sw[1:]))
+
+
+def _blocks_and_chains(Q, H):
+    """Upsilon(Q) as the walk's consumers run it: 2^H blocks of Upsilon(Q-H),
+    block b shifted by popcount(b), the chain after block b of level L =
+    trailing ones of b, [Q-H+L .. 1] shifted by popcount(b >> (L+1))."""
+    blk = seq.greedy_swaps(Q - H)
+    rows = []
+    for b in range(1 << H):
+        o = bin(b).count("1")
+        rows += [i + o for i in blk]
+        if b + 1 == (1 << H):
+            break
+        L = ((~b) & -(~b)).bit_length() - 1
+        oc = bin(b >> (L + 1)).count("1")
+        rows += [oc + j for j in range(Q - H + L, 0, -1)]
+    return rows
+
+
+@pytest.mark.parametrize("Q", range(3, 13))
+def test_recursion_splits_into_shifted_blocks(Q):
+    """Algorithm 1's recursion applied H times: the concatenation of shifted
+    blocks and chains is the greedy sequence itself."""
+    for H in range(1, Q - 1):
+        assert _blocks_and_chains(Q, H) == seq.greedy_swaps(Q)
