@@ -149,10 +149,34 @@ constexpr StepTab<Q> make_step_tab() {
 template <int Q>
 inline constexpr StepTab<Q> kSteps = make_step_tab<Q>();
 
+// Per step t and column bit jj (0..Q-1 a free variable, Q a fixed one): the
+// prefix mask compressed for that column's child block, or kNotChild when
+// the column's variable is itself in the prefix.
+constexpr uint16_t kNotChild = 0xffff;
+template <int Q>
+struct SlotTab {
+    static constexpr int N = StepTab<Q>::N;
+    uint16_t v[(N > 0 ? N : 1) * (Q + 1)];
+};
+template <int Q>
+constexpr SlotTab<Q> make_slot_tab() {
+    SlotTab<Q> tab{};
+    const StepTab<Q> st = make_step_tab<Q>();
+    for (int t = 0; t < StepTab<Q>::N; ++t)
+        for (int jj = 0; jj <= Q; ++jj) {
+            const unsigned pre = st.pre[t], lm = (1u << jj) - 1u;
+            tab.v[t * (Q + 1) + jj] = ((pre >> jj) & 1u)
+                                          ? kNotChild
+                                          : (uint16_t)((pre & lm) | ((pre >> 1) & ~lm));
+        }
+    return tab;
+}
+
 #ifdef GBN_Q
 // The step table of this translation unit's Q in constant memory (the
-// producer's rows, the consumers' run-time prefix masks).
+// producer's rows), and the consumers' compressed slot table.
 __constant__ StepTab<GBN_Q> c_steps = make_step_tab<GBN_Q>();
+__constant__ SlotTab<GBN_Q> c_slots = make_slot_tab<GBN_Q>();
 #endif
 
 __device__ __forceinline__ float wk_rsqrt(float x) { return rsqrtf(x); }
@@ -501,11 +525,15 @@ __device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
         const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
         emit_ptr<T, COV>(a, base, cT << sh, w[s], fma(T(s), a.lnn, penb), on && child);
     });
-    // one step at row i (absolute), tape step t; the mask from the table
+    // one step at row i (absolute), tape step t; the compressed slot from the
+    // table.  After an expired wait the remaining stores may hold stale scores;
+    // the status word reports it.
+    const uint16_t* slots = c_slots.v + jj;
     auto step = [&](auto& zz, auto& ww, int i_local, auto ic, int t, T pen_base, bool& ok) {
         constexpr int i = decltype(ic)::value;
         (void)i_local;
-        const unsigned pre = c_steps.pre[t];
+        (void)ok;
+        const unsigned cT = slots[t * (Q + 1)];
         const auto cs = tape[(size_t)t * 32 + ell];
         const T x = zz[i], y = zz[i + 1];
         zz[i] = fma(cs.x, x, cs.y * y);
@@ -513,9 +541,8 @@ __device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
         zz[i + 1] = yn;
         const T wn = fma(yn, yn, ww[i + 2]);
         ww[i + 1] = wn;
-        const bool child = !((pre >> jj) & 1u);
-        const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
-        emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, pen_base), on && child && ok);
+        emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, pen_base),
+                         on && cT != kNotChild);
     };
     auto wait_for = [&](int t, bool& ok) {  // tape steps t .. t + kChunk - 1 are written
         int c = (t + kChunk - 1) / kChunk;

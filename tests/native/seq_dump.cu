@@ -18,7 +18,16 @@ void dump_runtime(int Q) {
     std::printf("U %d %d\n", Q, gbn::upsilon_at(Q, n));  // past the end: 0
 }
 
+// The consumers' compressed slot table: "S Q t jj value"
+template <int Q>
+void dump_slots() {
+    constexpr auto tab = gbn::make_slot_tab<Q>();
+    for (int t = 0; t < gbn::StepTab<Q>::N; ++t)
+        for (int jj = 0; jj <= Q; ++jj) std::printf("S %d %d %d %u\n", Q, t, jj, (unsigned)tab.v[t * (Q + 1) + jj]);
+}
+
 int main() {
+    dump_slots<3>(); dump_slots<5>(); dump_slots<7>(); dump_slots<8>();
     for (int Q = 2; Q <= 14; ++Q) dump_runtime(Q);
     dump<2>(); dump<3>(); dump<4>(); dump<5>(); dump<6>(); dump<7>(); dump<8>();
     dump<9>(); dump<10>(); dump<11>(); dump<12>();

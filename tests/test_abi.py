@@ -7,6 +7,7 @@ import subprocess
 
 import pytest
 
+import oracle
 import oracle.sequence as seq
 from paper_1901_07643_gb300 import binding
 from paper_1901_07643_gb300 import build as gbn_build
@@ -83,7 +84,18 @@ def test_device_swap_tables_match_greedy_swaps(tmp_path):
     subprocess.run([gbn_build._nvcc(), "-std=c++17", "--expt-relaxed-constexpr", "-o", str(exe),
                     src], check=True, capture_output=True)
     lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
-    rows = [list(map(int, ln.split())) for ln in lines if not ln.startswith("U ")]
+    rows = [list(map(int, ln.split())) for ln in lines if not ln[0] in "US"]
+    slots = [list(map(int, ln.split()[1:])) for ln in lines if ln.startswith("S ")]
+    for Q in (3, 5, 7, 8):
+        sw = seq.greedy_swaps(Q)
+        orders = seq.apply_swaps(list(range(Q)), sw)[1:]
+        got = {(r[1], r[2]): r[3] for r in slots if r[0] == Q}
+        assert len(got) == len(sw) * (Q + 1)
+        for t, (o, i) in enumerate(zip(orders, sw)):
+            pre = sum(1 << v for v in o[:i])
+            for jj in range(Q + 1):
+                want = 0xFFFF if (pre >> jj) & 1 else oracle.compress(pre, jj)
+                assert got[(t, jj)] == want, (Q, t, jj)
     run = [list(map(int, ln.split()[1:])) for ln in lines if ln.startswith("U ")]
     for Q in range(2, 15):
         got = [r[1] for r in run if r[0] == Q]
