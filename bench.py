@@ -93,7 +93,7 @@ def _peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def _traffic(workload_name):
+def _traffic(workload_name, q=None):
     """Per-launch DRAM bytes of the walk kernel from the committed ncu summary, if current."""
     try:
         with open(TRAFFIC_FILE) as f:
@@ -101,6 +101,8 @@ def _traffic(workload_name):
     except Exception:
         return None
     if d.get("source_hash") != _source_hash() or d.get("workload") != workload_name:
+        return None
+    if q is not None and d.get("q") != q:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -459,7 +461,7 @@ def run_ours(args):
         "speedup_fp32_vs_fp64": (value / world) / fp64["value"] if fp64 else None,
         "walk_ms": walk_mean,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": _traffic(w.name),
+                     "frac": achieved / peak, "traffic": _traffic(w.name, q32 or binding.auto_q(w.m, 0)),
                      "peak_kind": peak_kind, "kernel": "walk_kernel",
                      "algorithmic_bytes_per_launch": algo_bytes},
         "cpu_baseline": cpu,

@@ -452,9 +452,15 @@ __device__ __forceinline__ bool replay(const WalkArgs<T>& a, const typename Vec2
         z[i + 1] = yn;
         const T wn = fma(yn, yn, w[i + 2]);
         w[i + 1] = wn;
+#ifdef GBN_Q
+        (void)pre;
+        const unsigned cT = c_slots.v[t * (Q + 1) + jj];
+        emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, penb), on && cT != kNotChild);
+#else
         const bool child = !((pre >> jj) & 1u);
         const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
         emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, penb), on && child && ok);
+#endif
     });
     return ok;
 }
