@@ -180,45 +180,67 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ gram, int p
             if (GBN_IN(chk, 123, i * kLd + i + q, 32 * kLd)) G[i * kLd + i + q] = s;
         }
     }
-    __syncthreads();
-    if (warp == 0) {
-        // right-looking Cholesky, lane l owns column l; row j of R replaces row j of G
-        for (int j = 0; j < m; ++j) {
-            const double d = G[j * kLd + j];
-            // one reciprocal square root per column; the row is scaled by it
-            const double inv = d > 0.0 ? rsqrt(d) : 0.0;
-            const double rjj = d * inv;
-            if (lane == 0 && !(d > 0.0)) atomicOr(status, GBN_STATUS_RANK_DEFICIENT);
-            __syncwarp();
-            if (lane >= j && lane < m)
-                G[j * kLd + lane] = (lane == j) ? rjj : G[j * kLd + lane] * inv;
-            __syncwarp();
-            if (lane > j && lane < m) {
-                const double rjl = G[j * kLd + lane];
-                for (int a = j + 1; a <= lane; ++a) G[a * kLd + lane] -= G[j * kLd + a] * rjl;
-            }
-            __syncwarp();
+    // pair table: pairs (a, b), a <= b, ordered by a, so that the pairs with
+    // a > j are a suffix starting at pair_start[j + 1]
+    __shared__ short2 pairs[32 * 33 / 2 + 1];
+    __shared__ int pair_start[33];
+    __shared__ double dinv[32];
+    if (tid <= m) {
+        int st = 0;
+        for (int a = 0; a < tid; ++a) st += m - a;
+        pair_start[tid] = st;
+    }
+    for (int e = tid; e < npair; e += blockDim.x) {
+        int q = e, a = 0;
+        while (q >= m - a) {
+            q -= m - a;
+            ++a;
         }
-        if (!R1 && Rinv_out) {
-            // column `lane` of R^{-1} by back substitution (zero pivots give zero entries)
-            if (lane < m) {
-                const double rl = G[lane * kLd + lane];
-                R1s[lane] = rl != 0.0 ? 1.0 / rl : 0.0;  // reciprocal of the diagonal
+        pairs[e] = make_short2((short)a, (short)(a + q));
+    }
+    __syncthreads();
+    // right-looking Cholesky over all threads: per column one reciprocal
+    // square root, the row scaled by it, then every trailing pair updated once
+    for (int j = 0; j < m; ++j) {
+        if (tid == 0) {
+            const double d = G[j * kLd + j];
+            const double inv = d > 0.0 ? rsqrt(d) : 0.0;
+            if (!(d > 0.0)) atomicOr(status, GBN_STATUS_RANK_DEFICIENT);
+            dinv[j] = inv;
+            G[j * kLd + j] = d * inv;
+        }
+        __syncthreads();
+        const double inv = dinv[j];
+        for (int l = j + 1 + tid; l < m; l += blockDim.x) G[j * kLd + l] *= inv;
+        __syncthreads();
+        for (int e = pair_start[j + 1] + tid; e < npair; e += blockDim.x) {
+            const short2 ab = pairs[e];
+            G[ab.x * kLd + ab.y] -= G[j * kLd + ab.x] * G[j * kLd + ab.y];
+        }
+        __syncthreads();
+    }
+    if (!R1 && Rinv_out) {
+        // R^{-1} right-looking from the last row: row j of X = B[j] / R_jj,
+        // then rows i < j of B lose R_ij * X[j] (B starts as I); zero pivots
+        // give zero rows
+        double* B = R1s;  // unused in this pass
+        for (int e = tid; e < 32 * kLd; e += blockDim.x) B[e] = 0.0;
+        __syncthreads();
+        for (int e = tid; e < m; e += blockDim.x) B[e * kLd + e] = 1.0;
+        __syncthreads();
+        for (int j = m - 1; j >= 0; --j) {
+            for (int c = j + tid; c < m; c += blockDim.x) B[j * kLd + c] *= dinv[j];
+            __syncthreads();
+            const int w = m - j;  // columns j .. m-1
+            for (int e = tid; e < j * w; e += blockDim.x) {
+                const int i = e / w, c = j + e % w;
+                B[i * kLd + c] -= G[i * kLd + j] * B[j * kLd + c];
             }
-            __syncwarp();
-            double x[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) x[i] = 0.0;
-            if (lane < m)
-                for (int i = lane; i >= 0; --i) {
-                    double s = (i == lane) ? 1.0 : 0.0;
-                    for (int l = i + 1; l <= lane; ++l) s -= G[i * kLd + l] * x[l];
-                    x[i] = s * R1s[i];
-                }
-            if (lane < m)
-                for (int i = 0; i < m; ++i)
-                    if (GBN_IN(chk, 126, i * m + lane, m * m))
-                        Rinv_out[i * m + lane] = (i <= lane) ? x[i] : 0.0;
+            __syncthreads();
+        }
+        for (int e = tid; e < m * m; e += blockDim.x) {
+            const int i = e / m, c = e % m;
+            if (GBN_IN(chk, 126, e, m * m)) Rinv_out[e] = (i <= c) ? B[i * kLd + c] : 0.0;
         }
     }
     __syncthreads();
