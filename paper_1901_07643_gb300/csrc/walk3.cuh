@@ -224,6 +224,28 @@ __device__ __forceinline__ void emit_ptr(const WalkArgs<T>& a, OutT<T, COV>* p, 
     }
 }
 
+// Store the score of the family at byte address base + cT * stride when
+// cT is a slot (not kNotChild) and `on` is set: one wide multiply-add forms
+// the address, and the predicate is built inside the store's own asm.
+__device__ __forceinline__ void st_slot(char* base, unsigned stride, unsigned cT, float v,
+                                        unsigned on) {
+    char* addr = base + (size_t)cT * stride;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %3, 0;\n\t"
+        "setp.ne.and.u32 p, %2, 65535, q;\n\t@p st.global.f32 [%0], %1;\n\t}"
+        :
+        : "l"(addr), "f"(v), "r"(cT), "r"(on));
+}
+__device__ __forceinline__ void st_slot(char* base, unsigned stride, unsigned cT, double v,
+                                        unsigned on) {
+    char* addr = base + (size_t)cT * stride;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %3, 0;\n\t"
+        "setp.ne.and.u32 p, %2, 65535, q;\n\t@p st.global.f64 [%0], %1;\n\t}"
+        :
+        : "l"(addr), "d"(v), "r"(cT), "r"(on));
+}
+
 // ---------------------------------------------------------------- mbarriers
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -535,6 +557,9 @@ __device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
     // table.  After an expired wait the remaining stores may hold stale scores;
     // the status word reports it.
     const uint16_t* slots = c_slots.v + jj;
+    char* const base_b = reinterpret_cast<char*>(base);
+    const unsigned stride = (unsigned)sizeof(OutT<T, COV>) << sh;
+    const unsigned on_u = on ? 1u : 0u;
     auto step = [&](auto& zz, auto& ww, int i_local, auto ic, int t, T pen_base, bool& ok) {
         constexpr int i = decltype(ic)::value;
         (void)i_local;
@@ -547,8 +572,19 @@ __device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
         zz[i + 1] = yn;
         const T wn = fma(yn, yn, ww[i + 2]);
         ww[i + 1] = wn;
-        emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, pen_base),
-                         on && cT != kNotChild);
+        if constexpr (COV) {
+            emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, pen_base),
+                             on && cT != kNotChild);
+        } else {
+#ifdef GBN_CHECKED
+            emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, pen_base),
+                             on && cT != kNotChild);
+#else
+            (void)base_b;
+            st_slot(base_b, stride, cT, fma(a.alpha, wk_log2(wn), fma(T(i + 1), a.lnn, pen_base)),
+                    on_u);
+#endif
+        }
     };
     auto wait_for = [&](int t, bool& ok) {  // tape steps t .. t + kChunk - 1 are written
         int c = (t + kChunk - 1) / kChunk;
@@ -688,6 +724,10 @@ __device__ __forceinline__ void consume(const WalkArgs<T>& a, const T* __restric
 namespace gbn {
 
 constexpr int kMaxConsumerWarps = 8;
+// Resident CTAs per SM the FP32 walk's register allocation must allow at 288
+// threads (56 registers); the FP64 walk is not bounded.
+template <typename T>
+constexpr int walk_min_blocks() { return std::is_same<T, float>::value ? 4 : 1; }
 
 template <typename T, int Q, bool COV>
 __device__ __forceinline__ void walk_body(const WalkArgs<T>& a, uint64_t cta) {
@@ -709,7 +749,8 @@ __device__ __forceinline__ void walk_body(const WalkArgs<T>& a, uint64_t cta) {
 }
 
 template <typename T, int Q, bool COV>
-__global__ void __launch_bounds__(32 * (1 + kMaxConsumerWarps)) walk_kernel(const WalkArgs<T> a) {
+__global__ void __launch_bounds__(32 * (1 + kMaxConsumerWarps), walk_min_blocks<T>())
+    walk_kernel(const WalkArgs<T> a) {
     walk_body<T, Q, COV>(a, blockIdx.x);
 }
 
