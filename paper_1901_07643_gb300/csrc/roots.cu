@@ -277,13 +277,17 @@ constexpr size_t stack_off() {
     return e;
 }
 
+// `node` is the saved copy of M: row j+1 of step j's pivot column is not yet
+// touched by the earlier rotations, so it is read from shared memory off the
+// critical path and only row j travels by shuffle.
 template <typename T, int RT, int rows>
-__device__ __forceinline__ void exclude_n(T (&M)[RT], T& C, int front, bool carried) {
+__device__ __forceinline__ void exclude_n(T (&M)[RT], T& C, int front, bool carried,
+                                          const T* node) {
     sfor(std::make_integer_sequence<int, rows - 1>{}, [&](auto jc) {
         constexpr int j = decltype(jc)::value;
         const int piv = front + 1 + j;
         const T a = __shfl_sync(0xffffffffu, M[j], piv);
-        const T b = __shfl_sync(0xffffffffu, M[j + 1], piv);
+        const T b = node[(j + 1) * 32 + piv];
         T c, s;
         givens_cs(a, b, c, s);
         const T x = M[j], y = M[j + 1];
@@ -369,7 +373,7 @@ struct Dfs5 {
                 } else {
                     load_n<T, RT, rows>(slot, M, C, carried, lane);
                     carried |= 1u << (topk + L);
-                    exclude_n<T, RT, rows>(M, C, topk + L, (carried >> lane) & 1u);
+                    exclude_n<T, RT, rows>(M, C, topk + L, (carried >> lane) & 1u, slot);
                 }
                 Dfs5<T, Q, L + 1>::run(M, C, carried, lane, topk, ell | (b << (W - 1 - L)), stack,
                                        p, rec, chk);
