@@ -237,6 +237,12 @@ __host__ __device__ __forceinline__ size_t dfs_stack_elems(int Q, int W) {
     return e > 0 ? e : 32;
 }
 
+// One warp's shared memory in the leaf kernel: the stack, then 8 staged
+// leaf records.
+__host__ __device__ __forceinline__ size_t warp_smem_elems(int Q, int W, size_t leaf_stride) {
+    return dfs_stack_elems(Q, W) + (leaf_stride / 32) * 8;
+}
+
 template <typename T>
 __device__ __forceinline__ void leaves_body(const T* __restrict__ top, const Plan& p,
                                             T* __restrict__ leaves, unsigned long long* chk,
@@ -352,6 +358,41 @@ __device__ __forceinline__ void write_leaf_q(const T (&M)[RT], T C, const Plan& 
     }
 }
 
+// Stage leaf ell's record in shared memory, stg[e * 8 + (ell & 7)]; after
+// the eighth leaf of a group (the enumeration runs ell = 31 down to 0) write
+// the group out as 8-float runs, one full 32-byte sector per record element.
+template <typename T, int Q, int RT>
+__device__ __forceinline__ void stage_leaf_q(const T (&M)[RT], T C, const Plan& p, int lane,
+                                             unsigned carried_mask, int ell, T* stg, T* rec,
+                                             unsigned long long* chk) {
+    constexpr int LQ = Q * (Q + 1) / 2;
+    const int k = p.k, j = ell & 7;
+    if (lane >= k && lane < p.m) {  // L column i: rows 0 .. i of the L block
+        const int i = lane - k;
+        const int e0 = i * (i + 1) / 2;
+        sfor(std::make_integer_sequence<int, Q>{}, [&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            if (r <= i) stg[(e0 + r) * 8 + j] = M[r];
+        });
+    } else if (lane < k && ((carried_mask >> lane) & 1u)) {  // fixed variable in B
+        const int e0 = LQ + var_of_lane(p, lane) * (Q + 1);
+        sfor(std::make_integer_sequence<int, Q>{}, [&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            stg[(e0 + r) * 8 + j] = M[r];
+        });
+        stg[(e0 + Q) * 8 + j] = C;
+    }
+    if (j == 0) {  // the group ell .. ell + 7 is complete
+        __syncwarp();
+        const int R = (int)(p.leaf_stride / 32);
+        for (int idx = lane; idx < R * 8; idx += 32) {
+            const size_t ix = (size_t)(idx >> 3) * 32 + ell + (idx & 7);
+            if (GBN_IN(chk, 227, ix, p.leaf_stride)) rec[ix] = stg[idx];
+        }
+        __syncwarp();
+    }
+}
+
 // Level L of the depth-first enumeration: save the node, then for each
 // choice of the level's variable (join F first, then join B) build the child
 // and descend.  One copy of each level's code.
@@ -362,7 +403,8 @@ struct Dfs5 {
                                                int topk, int ell, T* stack, const Plan& p, T* rec,
                                                unsigned long long* chk) {
         if constexpr (L == W) {
-            write_leaf_q<T, Q, RT>(M, C, p, lane, carried, ell, rec, chk);
+            stage_leaf_q<T, Q, RT>(M, C, p, lane, carried, ell, stack + stack_off<RT, W>(), rec,
+                                   chk);
         } else {
             T* slot = stack + stack_off<RT, L>();
             save_n<T, RT, rows>(slot, M, C, carried, lane);
@@ -435,7 +477,7 @@ __global__ void __launch_bounds__(32 * kDfsWarps) roots_leaves_kernel(const Plan
     const int warp = threadIdx.x >> 5;
     const uint64_t cta = (uint64_t)blockIdx.x * kDfsWarps + warp;
     if (cta >= (uint64_t)p.n_cta) return;
-    T* stack = reinterpret_cast<T*>(smem_raw) + warp * dfs_stack_elems(p.Q, p.W);
+    T* stack = reinterpret_cast<T*>(smem_raw) + warp * warp_smem_elems(p.Q, p.W, p.leaf_stride);
     T* leaves = reinterpret_cast<T*>(ws + p.off_leaves);
     unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
     if (!leaves_fast<T>(top_nodes<T>(p, ws), p, leaves, chk, cta, stack))
@@ -460,7 +502,8 @@ __global__ void __launch_bounds__(32 * kTopWarps) roots_top_kernel_b(const Batch
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kDfsWarps) roots_leaves_kernel_b(const BatchView v,
-                                                                         int Q, int max_w) {
+                                                                         int Q, int max_w,
+                                                                         size_t max_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
     const int64_t g = (int64_t)blockIdx.x * kDfsWarps + warp;
@@ -469,7 +512,7 @@ __global__ void __launch_bounds__(32 * kDfsWarps) roots_leaves_kernel_b(const Ba
     const int d = batch_locate(v, v.cta_prefix, g, local);
     const Plan& p = v.plans[d];
     char* ws = v.ws[d];
-    T* stack = reinterpret_cast<T*>(smem_raw) + warp * dfs_stack_elems(Q, max_w);
+    T* stack = reinterpret_cast<T*>(smem_raw) + warp * warp_smem_elems(Q, max_w, max_stride);
     T* leaves = reinterpret_cast<T*>(ws + p.off_leaves);
     unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
     if (!leaves_fast<T>(top_nodes<T>(p, ws), p, leaves, chk, (uint64_t)local, stack))
@@ -489,7 +532,8 @@ int roots_attr(size_t smem) {
 template <typename T>
 int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
     if (p.Q + p.W > kDfsRows) return GBN_ERR_Q;
-    const size_t smem = sizeof(T) * dfs_stack_elems(p.Q, p.W) * kDfsWarps;
+    const size_t smem = sizeof(T) * warp_smem_elems(p.Q, p.W, p.leaf_stride) * kDfsWarps;
+    if (smem > 227 * 1024) return GBN_ERR_Q;
     if (roots_attr<T>(smem)) return GBN_ERR_CUDA;
     const unsigned nb_top = (unsigned)((p.n_cta + kTopWarps - 1) / kTopWarps);
     const unsigned nb_dfs = (unsigned)((p.n_cta + kDfsWarps - 1) / kDfsWarps);
@@ -500,14 +544,15 @@ int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
 
 template <typename T>
 int launch_roots_batched_t(const BatchView& v, int64_t total_cta, int Q, int max_w,
-                           cudaStream_t stream) {
+                           size_t max_stride, cudaStream_t stream) {
     if (Q + max_w > kDfsRows) return GBN_ERR_Q;
-    const size_t smem = sizeof(T) * dfs_stack_elems(Q, max_w) * kDfsWarps;
+    const size_t smem = sizeof(T) * warp_smem_elems(Q, max_w, max_stride) * kDfsWarps;
+    if (smem > 227 * 1024) return GBN_ERR_Q;
     if (roots_attr<T>(smem)) return GBN_ERR_CUDA;
     const unsigned nb_top = (unsigned)((total_cta + kTopWarps - 1) / kTopWarps);
     const unsigned nb_dfs = (unsigned)((total_cta + kDfsWarps - 1) / kDfsWarps);
     roots_top_kernel_b<T><<<nb_top, 32 * kTopWarps, 0, stream>>>(v);
-    roots_leaves_kernel_b<T><<<nb_dfs, 32 * kDfsWarps, smem, stream>>>(v, Q, max_w);
+    roots_leaves_kernel_b<T><<<nb_dfs, 32 * kDfsWarps, smem, stream>>>(v, Q, max_w, max_stride);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
@@ -525,9 +570,8 @@ int launch_roots(const Plan& p, char* ws, cudaStream_t stream) {
 
 int launch_roots_batched(const BatchView& v, int64_t total_cta, int Q, int max_w,
                          size_t max_stride, int precision, cudaStream_t stream) {
-    (void)max_stride;
-    return precision ? launch_roots_batched_t<double>(v, total_cta, Q, max_w, stream)
-                     : launch_roots_batched_t<float>(v, total_cta, Q, max_w, stream);
+    return precision ? launch_roots_batched_t<double>(v, total_cta, Q, max_w, max_stride, stream)
+                     : launch_roots_batched_t<float>(v, total_cta, Q, max_w, max_stride, stream);
 }
 
 }  // namespace gbn
