@@ -37,7 +37,8 @@ WALK_SOURCES = ["paper_1901_07643_gb300/csrc/walk3.cuh", "paper_1901_07643_gb300
                 "paper_1901_07643_gb300/csrc/walk_dispatch.cu",
                 "paper_1901_07643_gb300/csrc/gbn_internal.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk_traffic.json")
-LAUNCHES_PER_STEP = 11  # colsum, mean, gram x2, cholesky x2, fix-up flags, roots, walk, fix-up scan + solve
+LAUNCHES_PER_STEP = 12  # colsum, mean, gram x2, cholesky x2, fix-up flags, roots top + leaves, walk,
+                        # fix-up scan + solve
 
 
 def _args():
@@ -91,6 +92,12 @@ def _peak_hbm():
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def _walk_kernel_name(m, q):
+    """The FP32 walk kernel a single-dataset call launches (the library's choice for full warps
+    of sub-walks and an even number of roots CTAs, which every bench workload has)."""
+    return f"walk_ring_kernel<{q}, true>" if q <= 6 else f"walk_kernel_pair<{q}>"
 
 
 def _traffic(workload_name, q=None):
@@ -479,7 +486,7 @@ def run_ours(args):
         "walk_ms": walk_mean,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": _traffic(w.name, q32 or binding.auto_q(w.m, 0)),
-                     "peak_kind": peak_kind, "kernel": "walk_kernel",
+                     "peak_kind": peak_kind, "kernel": _walk_kernel_name(w.m, q32 or binding.auto_q(w.m, 0)),
                      "algorithmic_bytes_per_launch": algo_bytes},
         "cpu_baseline": cpu,
         "e2e": e2e,

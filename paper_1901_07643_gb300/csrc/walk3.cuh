@@ -36,6 +36,17 @@
 // Scores: score = n ln(RSS/n) + |S| ln n = (n ln 2) log2(RSS) + (|S| ln n - n ln n),
 // stored at idx(c,S) = c 2^(m-1) + compress(S, c); the lanes of a warp write
 // consecutive table slots.
+//
+// FP32 scores with full warps of sub-walks take one of two refinements:
+//   * the paired walk: one block runs the sub-walks of two neighbouring roots
+//     CTAs (front sets differing in fixed variable W).  Two producer warps
+//     write one interleaved tape (c0, c1, s0, s1); a consumer lane holds a
+//     column of both sub-walks in float2 registers and rotates, sums and
+//     scores them with packed FP32 instructions, so the walk issues about
+//     16 instead of 24 instructions per family;
+//   * the paired ring (Q <= 6): the same pairs in persistent blocks with two
+//     tapes in shared memory, so one pair's tape is written while the
+//     consumers replay the previous one.
 #pragma once
 
 #include <type_traits>
@@ -181,7 +192,13 @@ __constant__ SlotTab<GBN_Q> c_slots = make_slot_tab<GBN_Q>();
 
 __device__ __forceinline__ float wk_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double wk_rsqrt(double x) { return rsqrt(x); }
-__device__ __forceinline__ float wk_log2(float x) { return __log2f(x); }
+// FP32: the hardware base-2 logarithm with subnormal inputs flushed to zero
+// (an RSS below 2^-126 scores -inf; the FP64 fix-up re-scores such families).
+__device__ __forceinline__ float wk_log2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double wk_log2(double x) { return log2(x); }
 __device__ __forceinline__ float2 wk_pair(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 wk_pair(double a, double b) { return make_double2(a, b); }
@@ -260,13 +277,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
             smem_addr(bar))
         : "memory");
 }
+// One poll; a thread whose phase is not complete is suspended until it
+// completes or kSuspendNs pass, so a waiting warp issues almost nothing.
+constexpr unsigned kSuspendNs = 20000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, "
+        "%3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -276,8 +296,7 @@ __device__ __forceinline__ long long global_ns() {
     return t;
 }
 // Bounded wait for the phase with the given parity; false = watchdog expired.
-// try_wait suspends the thread for a short hardware-defined time when the
-// phase is not complete; the clock is read only every 64 polls.
+// The clock is read only every 64 polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit_ns,
                                           int* status) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -354,6 +373,17 @@ struct Smem {
     static constexpr size_t bytes = off_bar + (size_t)chunks * sizeof(uint64_t);
 };
 
+// Shared memory of the paired walk: a tape of (c0, c1, s0, s1) per step and
+// lane (FP32), then the chunk barriers (two producer arrivals each).
+template <int Q>
+struct SmemP {
+    static constexpr int N = StepTab<Q>::N;
+    static constexpr int chunks = (N + kChunk - 1) / kChunk;
+    static constexpr size_t off_tape = 0;
+    static constexpr size_t off_bar = (size_t)N * 32 * 4 * sizeof(float);
+    static constexpr size_t bytes = off_bar + (size_t)chunks * sizeof(uint64_t);
+};
+
 // One swap of the producer at compile-time row I.  R is named by position:
 // R[r * Q + p] (r <= p) is row r of the column at position p.
 template <typename T, int Q, int I>
@@ -385,16 +415,21 @@ __device__ __forceinline__ void produce_step(T (&R)[Q * Q], T& c_out, T& s_out) 
     s_out = s;
 }
 
-// Producer: one sub-walk per lane over its free block, rotations only.
-template <typename T, int Q>
+// Producer: one sub-walk per lane over its free block, rotations only.  It
+// stays a state machine: a version unrolled over all 2^Q - Q - 1 steps (swaps
+// as register renames, no row table) measured 20-30 % slower at Q = 6, 7 --
+// its code does not stay in the instruction cache beside the consumers'.
+// SLOT < 0: the tape holds (c, s) per step and lane.  SLOT 0 or 1: two
+// producers share a tape of (c0, c1, s0, s1) per step and lane (the paired
+// walk), this one writing component SLOT of each pair.
+template <typename T, int Q, int SLOT = -1>
 __device__ __forceinline__ void produce(const WalkArgs<T>& a, const StepTab<Q>& tab,
-                                        const T* __restrict__ rec, unsigned char* smem, int lane,
-                                        bool active) {
-    using S = Smem<T, Q>;
+                                        const T* __restrict__ rec, unsigned char* tape_base,
+                                        uint64_t* full, int lane, bool active) {
     using T2 = typename Vec2T<T>::type;
     constexpr int N = StepTab<Q>::N;
-    T2* tape = reinterpret_cast<T2*>(smem + S::off_tape);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::off_bar);
+    T2* tape = reinterpret_cast<T2*>(tape_base);
+    T* tape4 = reinterpret_cast<T*>(tape_base);
     T R[Q * Q];
     static_for(std::make_integer_sequence<int, Q>{}, [&](auto pc) {
         constexpr int p = decltype(pc)::value;
@@ -410,7 +445,12 @@ __device__ __forceinline__ void produce(const WalkArgs<T>& a, const StepTab<Q>& 
 #define GBN_PSTEP(r, UP, DOWN)                                                     \
     if (r < Q - 1) {                                                               \
         produce_step<T, Q, (r < Q - 1 ? r : 0)>(R, c, s);                          \
-        tape[t * 32 + lane] = wk_pair(c, s);                                       \
+        if constexpr (SLOT < 0) {                                                  \
+            tape[t * 32 + lane] = wk_pair(c, s);                                   \
+        } else {                                                                   \
+            tape4[(t * 32 + lane) * 4 + SLOT] = c;                                 \
+            tape4[(t * 32 + lane) * 4 + 2 + SLOT] = s;                             \
+        }                                                                          \
         if (++t == N) goto p_done;                                                 \
         if (t % kChunk == 0) {                                                     \
             __syncwarp();                                                          \
@@ -443,7 +483,8 @@ p_done:
 // the table slot.  Returns false if a wait expired.
 template <typename T, int Q, bool COV>
 __device__ __forceinline__ bool replay(const WalkArgs<T>& a, const typename Vec2T<T>::type* tape,
-                                       uint64_t* full, T (&z)[Q], T cres, int ell, int jj, int sh,
+                                       uint64_t* full, unsigned par, T (&z)[Q], T cres, int ell,
+                                       int jj, int sh,
                                        OutT<T, COV>* base, T penb, bool on) {
     constexpr int N = StepTab<Q>::N;
     T w[Q + 1];
@@ -463,7 +504,7 @@ __device__ __forceinline__ bool replay(const WalkArgs<T>& a, const typename Vec2
     static_for(std::make_integer_sequence<int, N>{}, [&](auto tc) {
         constexpr int t = decltype(tc)::value;
         if constexpr (t % kChunk == 0) {
-            if (ok) ok = warp_wait(&full[t / kChunk], 0, a.watchdog_ns, a.status);
+            if (ok) ok = warp_wait(&full[t / kChunk], par, a.watchdog_ns, a.status);
         }
         constexpr int i = kSteps<Q>.row[t];
         constexpr unsigned pre = kSteps<Q>.pre[t];
@@ -497,35 +538,51 @@ __device__ __forceinline__ bool replay(const WalkArgs<T>& a, const typename Vec2
 // register view; each (chain length, shift) pair has one unrolled copy; the
 // prefix masks come from the constant step table at run time.  The walk is
 // bound by instruction fetch, so shrinking its code pays for the table load.
+// Calls f(integral_constant<OO>) for exactly one OO in 0 .. NB: OO = x, or NB
+// when x >= NB.  Every path takes one branch, so a value written in all of
+// them is known to be overwritten (a plain "if (x == OO)" per OO leaves a
+// path with none taken and keeps the old values alive in registers).
+template <int OO, int NB, class F>
+__device__ __forceinline__ void pick_from(int x, F&& f) {
+    if constexpr (OO == NB) {
+        f(std::integral_constant<int, OO>{});
+    } else {
+        if (x == OO)
+            f(std::integral_constant<int, OO>{});
+        else
+            pick_from<OO + 1, NB>(x, f);
+    }
+}
+template <int NB, class F>
+__device__ __forceinline__ void pick(int x, F&& f) {
+    pick_from<0, NB>(x, f);
+}
+
 template <int Q1, int NB>
 struct ViewCopy {  // zv/wv <-> z/w rows o .. o + Q1 (o a run-time shift 0 .. NB)
     template <typename T, int Q>
     __device__ static __forceinline__ void in(T (&zv)[Q1], T (&wv)[Q1 + 1], const T (&z)[Q],
                                               const T (&w)[Q + 1], int o) {
-        static_for(std::make_integer_sequence<int, NB + 1>{}, [&](auto oc) {
+        pick<NB>(o, [&](auto oc) {
             constexpr int oo = decltype(oc)::value;
-            if (o == oo) {
-                static_for(std::make_integer_sequence<int, Q1>{}, [&](auto rc) {
-                    constexpr int r = decltype(rc)::value;
-                    zv[r] = z[r + oo];
-                    wv[r] = w[r + oo];
-                });
-                wv[Q1] = w[Q1 + oo];
-            }
+            static_for(std::make_integer_sequence<int, Q1>{}, [&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                zv[r] = z[r + oo];
+                wv[r] = w[r + oo];
+            });
+            wv[Q1] = w[Q1 + oo];
         });
     }
     template <typename T, int Q>
     __device__ static __forceinline__ void out(const T (&zv)[Q1], const T (&wv)[Q1 + 1], T (&z)[Q],
                                                T (&w)[Q + 1], int o) {
-        static_for(std::make_integer_sequence<int, NB + 1>{}, [&](auto oc) {
+        pick<NB>(o, [&](auto oc) {
             constexpr int oo = decltype(oc)::value;
-            if (o == oo) {
-                static_for(std::make_integer_sequence<int, Q1>{}, [&](auto rc) {
-                    constexpr int r = decltype(rc)::value;
-                    z[r + oo] = zv[r];
-                    w[r + oo] = wv[r];
-                });
-            }
+            static_for(std::make_integer_sequence<int, Q1>{}, [&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                z[r + oo] = zv[r];
+                w[r + oo] = wv[r];
+            });
         });
     }
 };
@@ -533,7 +590,7 @@ struct ViewCopy {  // zv/wv <-> z/w rows o .. o + Q1 (o a run-time shift 0 .. NB
 template <typename T, int Q, int H, bool COV>
 __device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
                                              const typename Vec2T<T>::type* tape, uint64_t* full,
-                                             T (&z)[Q], T cres, int ell, int jj, int sh,
+                                             unsigned par, T (&z)[Q], T cres, int ell, int jj, int sh,
                                              OutT<T, COV>* base, T penb, bool on) {
     static_assert(Q == GBN_Q, "the step table in constant memory is this unit's");
     static_assert(H >= 1 && Q - H >= 2, "blocks of at least two variables");
@@ -589,7 +646,7 @@ __device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
     auto wait_for = [&](int t, bool& ok) {  // tape steps t .. t + kChunk - 1 are written
         int c = (t + kChunk - 1) / kChunk;
         if (c > last_chunk) c = last_chunk;
-        if (ok) ok = warp_wait(&full[c], 0, a.watchdog_ns, a.status);
+        if (ok) ok = warp_wait(&full[c], par, a.watchdog_ns, a.status);
     };
     bool ok = true;
     int t0 = 0;  // tape step of the current block's first step
@@ -634,27 +691,221 @@ __device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
 }
 #endif
 
-// Consumers: the CTA's columns, item it -> warp (it mod n_cwarps).
+#ifdef GBN_Q
+// ---------------------------------------------------------------- paired walk
+// Two sub-walks per lane: those of two neighbouring roots CTAs (front sets
+// differing in fixed variable W only).  The rotations of both come from one
+// tape entry (c0, c1, s0, s1), a column's entries of both sub-walks sit in
+// one float2, and every rotation, tail sum and score is one packed FP32
+// operation for the two families; the two scores go to slots a constant
+// byte distance apart.  Same block/chain structure as replay_split.
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+template <int Q, int H>
+__device__ __forceinline__ bool replay_pair(const WalkArgs<float>& a, const float4* tape,
+                                            uint64_t* full, unsigned par, float2 (&z)[Q], float2 cres,
+                                            int ell,
+                                            int jj, int sh, char* base, unsigned off1, float2 penb,
+                                            unsigned on0, unsigned on1) {
+    static_assert(Q == GBN_Q, "the step tables in constant memory are this unit's");
+    constexpr int N = StepTab<Q>::N;
+    constexpr int last_chunk = (N - 1) / kChunk;
+    constexpr int QB = Q - H;
+    constexpr int NBLK = StepTab<QB>::N;
+    float2 w[Q + 1];
+    w[Q] = cres;
+#pragma unroll
+    for (int r = Q - 1; r >= 0; --r) w[r] = __ffma2_rn(z[r], z[r], w[r + 1]);
+    const float2 alpha2 = f2(a.alpha), lnn2 = f2(a.lnn);
+    const unsigned stride = 4u << sh;
+    const unsigned lm = (1u << jj) - 1u;
+    auto emit2 = [&](unsigned cT, float2 rss, float2 pen) {
+        const float2 lg = make_float2(wk_log2(rss.x), wk_log2(rss.y));
+        const float2 sc = __ffma2_rn(alpha2, lg, pen);
+#ifdef GBN_CHECKED
+        if (cT != kNotChild) {
+            const size_t e0 = (size_t)(base - reinterpret_cast<char*>(a.out)) / 4 +
+                              (size_t)cT * (stride / 4);
+            if (on0 && GBN_IN(a.chk, 332, e0, a.out_size))
+                *reinterpret_cast<float*>(base + (size_t)cT * stride) = sc.x;
+            if (on1 && GBN_IN(a.chk, 333, e0 + off1 / 4, a.out_size))
+                *reinterpret_cast<float*>(base + off1 + (size_t)cT * stride) = sc.y;
+        }
+#else
+        st_slot(base, stride, cT, sc.x, on0);
+        st_slot(base + off1, stride, cT, sc.y, on1);
+#endif
+    };
+    static_for(std::make_integer_sequence<int, Q + 1>{}, [&](auto sc) {  // the roots' families
+        constexpr int s = decltype(sc)::value;
+        constexpr unsigned pre = (1u << s) - 1u;
+        const unsigned cT = ((pre >> jj) & 1u) ? kNotChild : ((pre & lm) | ((pre >> 1) & ~lm));
+        emit2(cT, w[s], __ffma2_rn(f2(float(s)), lnn2, penb));
+    });
+    const uint16_t* slots = c_slots.v + jj;
+    auto step = [&](auto& zz, auto& ww, auto ic, int t, float2 pen_base) {
+        constexpr int i = decltype(ic)::value;
+        const unsigned cT = slots[t * (Q + 1)];
+        const float4 cs = tape[(size_t)t * 32 + ell];
+        const float2 c2 = make_float2(cs.x, cs.y), s2 = make_float2(cs.z, cs.w);
+        const float2 x = zz[i], y = zz[i + 1];
+        zz[i] = __ffma2_rn(c2, x, __fmul2_rn(s2, y));
+        const float2 sx = __fmul2_rn(s2, x);
+        const float2 yn = __ffma2_rn(c2, y, make_float2(-sx.x, -sx.y));
+        zz[i + 1] = yn;
+        const float2 wn = __ffma2_rn(yn, yn, ww[i + 2]);
+        ww[i + 1] = wn;
+        emit2(cT, wn, __ffma2_rn(f2(float(i + 1)), lnn2, pen_base));
+    };
+    auto wait_for = [&](int t, bool& ok) {
+        int c = (t + kChunk - 1) / kChunk;
+        if (c > last_chunk) c = last_chunk;
+        if (ok) ok = warp_wait(&full[c], par, a.watchdog_ns, a.status);
+    };
+    bool ok = true;
+    int t0 = 0;
+#pragma unroll 1
+    for (int b = 0; b < (1 << H); ++b) {
+        const int o = __popc(b);
+        float2 zv[QB], wv[QB + 1];
+        ViewCopy<QB, H>::template in<float2, Q>(zv, wv, z, w, o);
+        const float2 penv = __ffma2_rn(f2(float(o)), lnn2, penb);
+        static_for(std::make_integer_sequence<int, NBLK>{}, [&](auto tc) {
+            constexpr int t = decltype(tc)::value;
+            if constexpr (t % kChunk == 0) wait_for(t0 + t, ok);
+            step(zv, wv, std::integral_constant<int, kSteps<QB>.row[t]>{}, t0 + t, penv);
+        });
+        ViewCopy<QB, H>::template out<float2, Q>(zv, wv, z, w, o);
+        t0 += NBLK;
+        if (b + 1 == (1 << H)) break;
+        const int L = __ffs(~b) - 1;
+        const int oc = __popc(b >> (L + 1));
+        wait_for(t0, ok);
+        static_for(std::make_integer_sequence<int, (H > 0 ? H : 1)>{}, [&](auto lc) {
+            constexpr int LL = decltype(lc)::value;
+            constexpr int len = QB + LL;
+            if (L == LL) {
+                static_for(std::make_integer_sequence<int, (H > LL ? H - LL : 1)>{}, [&](auto occ) {
+                    constexpr int OO = decltype(occ)::value;
+                    if (oc == OO) {
+                        static_for(std::make_integer_sequence<int, len>{}, [&](auto uc) {
+                            constexpr int u = decltype(uc)::value;
+                            constexpr int i = OO + len - 1 - u;
+                            if constexpr (i + 1 < Q)
+                                step(z, w, std::integral_constant<int, i>{}, t0 + u, penb);
+                        });
+                    }
+                });
+                t0 += len;
+            }
+        });
+    }
+    return ok;
+}
+
+// Consumers of the paired walk.  Items: the Q free variables; the fixed
+// variables above W outside the pair's front sets (both sub-walks); fixed
+// variable W (the first sub-walk only: it is in the second one's front set);
+// the lowest W variables in lane groups (both sub-walks).
+// The warp takes items first, first + stride, ...; returns the number of
+// items of the pair, or -1 when a wait expired.
+template <int Q>
+__device__ __forceinline__ int consume_pair(const WalkArgs<float>& a, const float* __restrict__ rec0,
+                                            const float* __restrict__ rec1, const float4* tape,
+                                            uint64_t* full, unsigned par, int lane, int first,
+                                            int stride, uint64_t pc) {
+    constexpr int LQ = Q * (Q + 1) / 2;
+    constexpr int H = split_levels(Q);
+    const int W = a.W;
+    const uint64_t Fhi0 = (pc << 1) << W;  // the first sub-walk's fixed bits above W
+    const int nu = (a.k - W - 1) - __popcll(pc);  // variables above W, outside both front sets
+    const int g = a.lanes >> 1;
+    const int vpi = 32 / g;
+    const int n5 = (W + vpi - 1) / vpi;
+    const int nitems = Q + nu + 1 + n5;
+    char* out = reinterpret_cast<char*>(a.out);
+    const float lnn = a.lnn;
+    // penalty bases of the two sub-walks, rounded as the single walk rounds them
+    auto pen2 = [&](uint64_t F0) {
+        const float c0 = float(__popcll(F0));
+        return make_float2(fmaf(c0, lnn, -a.nlnn), fmaf(c0 + 1.f, lnn, -a.nlnn));
+    };
+    // entry ix of both records (the second one is never past the first's stride)
+    auto ld2 = [&](size_t ix, bool on, int site) {
+        return (on && GBN_IN(a.chk, site, ix, a.leaf_stride)) ? make_float2(rec0[ix], rec1[ix])
+                                                             : make_float2(0.f, 0.f);
+    };
+    auto load2 = [&](float2 (&z)[Q], float2& cres, size_t e_base, int ell, bool on) {
+#pragma unroll
+        for (int e = 0; e < Q; ++e) z[e] = ld2(e_base + (size_t)e * 32 + ell, on, 331);
+        cres = ld2(e_base + (size_t)Q * 32 + ell, on, 331);
+    };
+    for (int it = first; it < nitems; it += stride) {
+        // the item's column, then one replay call site (its code is the walk's size)
+        float2 z[Q], cres = make_float2(0.f, 0.f);
+        int ell = lane, jj = Q, sh = a.k - 1;
+        unsigned off1, on0 = 1u, on1 = 1u;
+        size_t slot0;  // table element of the first sub-walk's prefix-0 family
+        if (it < Q) {  // free variable j
+            const int j = it;
+#pragma unroll
+            for (int e = 0; e < Q; ++e)
+                z[e] = ld2((size_t)(j * (j + 1) / 2 + e) * 32 + lane, e <= j, 330);
+            jj = j;
+            sh = a.k;
+            off1 = 4u << W;
+            slot0 = ((size_t)(a.k + j) << (a.m - 1)) + (Fhi0 | (uint64_t)lane);
+        } else {  // a fixed variable v outside the front sets
+            int v;
+            bool on = true;
+            if (it < Q + nu + 1) {  // above W, or W itself (the first sub-walk only)
+                const int idx = it - Q;
+                v = idx < nu ? W + 1 + nth_zero_bit(pc, idx) : W;
+                off1 = v > W ? (4u << W) : 0u;
+                on1 = v > W ? 1u : 0u;
+            } else {  // the lowest W variables, a group of lanes each
+                const int j = it - Q - nu - 1;
+                const int uu = lane / g, sub = lane % g;
+                v = j * vpi + uu;
+                on = v < W;
+                ell = on ? ((sub & ((1 << v) - 1)) | ((sub >> v) << (v + 1))) : 0;
+                if (!on) v = 0;
+                off1 = 4u << (W - 1);
+                on0 = on1 = on ? 1u : 0u;
+            }
+            load2(z, cres, (size_t)32 * (LQ + v * (Q + 1)), ell, on);
+            const uint64_t F0 = Fhi0 | (uint64_t)ell;
+            const uint64_t lowmask = (1ull << v) - 1ull;
+            slot0 = ((size_t)v << (a.m - 1)) + ((F0 & lowmask) | ((F0 >> (v + 1)) << v));
+        }
+        const bool ok = replay_pair<Q, H>(a, tape, full, par, z, cres, ell, jj, sh,
+                                          out + slot0 * 4, off1, pen2(Fhi0 | (uint64_t)ell), on0,
+                                          on1);
+        if (!ok) return -1;
+    }
+    return nitems;
+}
+#endif
+
+// Consumers: the CTA's columns; the warp takes items first, first + stride, ...
+// and returns the CTA's item count (-1 when a wait expired).
 //   items [0, Q)             free variable j = it, every lane;
 //   items [Q, Q + nu)        the fixed variables above the lowest W outside F_hi;
 //   items [Q + nu, + n5)     the lowest W variables, 32/g per item, g = 2^(W-1)
 //                            lanes each (only sub-walks without it in F).
 template <typename T, int Q, bool COV>
-__device__ __forceinline__ void consume(const WalkArgs<T>& a, const T* __restrict__ rec,
-                                        unsigned char* smem, int lane, int cw, uint64_t cta,
-                                        uint64_t Fhi) {
-    using S = Smem<T, Q>;
-    using T2 = typename Vec2T<T>::type;
+__device__ __forceinline__ int consume(const WalkArgs<T>& a, const T* __restrict__ rec,
+                                       const typename Vec2T<T>::type* tape, uint64_t* full,
+                                       unsigned par, int lane, int first, int stride, uint64_t cta,
+                                       uint64_t Fhi) {
     constexpr int LQ = Q * (Q + 1) / 2;
-    const T2* tape = reinterpret_cast<const T2*>(smem + S::off_tape);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::off_bar);
     const int nu = (a.k - a.W) - __popcll(cta);
     const int g = a.W >= 1 ? (a.lanes >> 1) : 1;
     const int vpi = 32 / g;
     const int n5 = a.W >= 1 ? (a.W + vpi - 1) / vpi : 0;
     const int nitems = Q + nu + n5;
     GBN_TIMER_DECL
-    for (int it = cw; it < nitems; it += a.n_cwarps) {
+    for (int it = first; it < nitems; it += stride) {
         T z[Q];
         int ell = lane, jj, sh;
         bool on;
@@ -706,14 +957,15 @@ __device__ __forceinline__ void consume(const WalkArgs<T>& a, const T* __restric
         bool ok;
 #ifdef GBN_Q
         if constexpr (split_levels(Q) > 0)
-            ok = replay_split<T, Q, split_levels(Q), COV>(a, tape, full, z, cres, ell, jj, sh, base,
-                                                        penb, on);
+            ok = replay_split<T, Q, split_levels(Q), COV>(a, tape, full, par, z, cres, ell, jj, sh,
+                                                        base, penb, on);
         else
 #endif
-            ok = replay<T, Q, COV>(a, tape, full, z, cres, ell, jj, sh, base, penb, on);
-        if (!ok) return;
+            ok = replay<T, Q, COV>(a, tape, full, par, z, cres, ell, jj, sh, base, penb, on);
+        if (!ok) return -1;
     }
     GBN_TIMER_FLUSH(a.timing, 1)
+    return nitems;
 }
 
 }  // namespace gbn
@@ -725,9 +977,12 @@ namespace gbn {
 
 constexpr int kMaxConsumerWarps = 8;
 // Resident CTAs per SM the FP32 walk's register allocation must allow at 288
-// threads (56 registers); the FP64 walk is not bounded.
-template <typename T>
-constexpr int walk_min_blocks() { return std::is_same<T, float>::value ? 4 : 1; }
+// threads: five up to Q = 7 (40 registers), three at Q = 8 (the tape's shared
+// memory allows no more); the FP64 walk is not bounded.
+template <typename T, int Q>
+constexpr int walk_min_blocks() {
+    return std::is_same<T, float>::value ? (Q <= 7 ? 5 : (Q == 8 ? 3 : 1)) : 1;
+}
 
 template <typename T, int Q, bool COV>
 __device__ __forceinline__ void walk_body(const WalkArgs<T>& a, uint64_t cta) {
@@ -743,13 +998,14 @@ __device__ __forceinline__ void walk_body(const WalkArgs<T>& a, uint64_t cta) {
     const uint64_t Fhi = cta << a.W;
     const T* rec = a.leaves + (size_t)cta * a.leaf_stride;
     if (warp == 0)
-        produce<T, Q>(a, c_steps, rec, smem, lane, lane < a.lanes);
+        produce<T, Q>(a, c_steps, rec, smem + S::off_tape, full, lane, lane < a.lanes);
     else
-        consume<T, Q, COV>(a, rec, smem, lane, warp - 1, cta, Fhi);
+        consume<T, Q, COV>(a, rec, reinterpret_cast<const typename Vec2T<T>::type*>(smem + S::off_tape),
+                           full, 0u, lane, warp - 1, a.n_cwarps, cta, Fhi);
 }
 
 template <typename T, int Q, bool COV>
-__global__ void __launch_bounds__(32 * (1 + kMaxConsumerWarps), walk_min_blocks<T>())
+__global__ void __launch_bounds__(32 * (1 + kMaxConsumerWarps), walk_min_blocks<T, Q>())
     walk_kernel(const WalkArgs<T> a) {
     walk_body<T, Q, COV>(a, blockIdx.x);
 }
@@ -764,10 +1020,187 @@ __global__ void __launch_bounds__(32 * (1 + kMaxConsumerWarps)) walk_kernel_b(co
     walk_body<T, Q, COV>(a, (uint64_t)local);
 }
 
+// The paired FP32 walk: block c runs the sub-walks of roots CTAs 2c and 2c+1
+// (W = 5).  Warps 0 and 1 produce the two halves of the tape, the others
+// consume both sub-walks at once.
+constexpr int kPairThreads = 32 * (2 + kMaxConsumerWarps);
+constexpr size_t kPairMaxSmem = 160 * 1024;  // the tape of Q = 9 does not fit
+template <int Q>
+__global__ void __launch_bounds__(kPairThreads, Q >= 8 ? 1 : 3) walk_kernel_pair(const WalkArgs<float> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    using S = SmemP<Q>;
+    static_assert(Q == GBN_Q, "one Q per translation unit");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::off_bar);
+    for (int c = threadIdx.x; c < S::chunks; c += blockDim.x) mbar_init(&full[c], 2);
+    __syncthreads();
+    const uint64_t pc = blockIdx.x;
+    const float* rec0 = a.leaves + (size_t)(2 * pc) * a.leaf_stride;
+    const float* rec1 = rec0 + a.leaf_stride;
+    if (warp == 0)
+        produce<float, Q, 0>(a, c_steps, rec0, smem + S::off_tape, full, lane, true);
+    else if (warp == 1)
+        produce<float, Q, 1>(a, c_steps, rec1, smem + S::off_tape, full, lane, true);
+    else
+        consume_pair<Q>(a, rec0, rec1, reinterpret_cast<const float4*>(smem + S::off_tape), full,
+                        0u, lane, warp - 2, a.n_cwarps, pc);
+}
+
+// Whether a launch takes the paired walk: FP32 scores, full warps of
+// sub-walks (W = 5) and an even number of roots CTAs.
+template <typename T, int Q, bool COV>
+constexpr bool pair_walk_compiled() {
+    return std::is_same<T, float>::value && !COV && SmemP<Q>::bytes <= kPairMaxSmem;
+}
+
+// ---------------------------------------------------------------- ring walk
+// A persistent form of the FP32 walk.  A unit is one roots CTA's 32
+// sub-walks (PAIR: two neighbouring ones, as in the paired walk); block b takes
+// units b, b + gridDim.x, ... and keeps a ring of two tapes in shared memory.
+// The producer warp(s) write the tape of the block's j-th unit into slot j mod 2
+// as soon as the consumers have released unit j - 2, so while the consumers
+// replay one unit the next unit's tape is being written: they do not wait for
+// a producer that starts when they do.  The consumer warps take the items of
+// successive units as one round-robin stream, so no warp idles at a unit's end
+// while another finishes a third item.
+template <int Q, bool PAIR>
+struct RingSmem {
+    static constexpr int N = StepTab<Q>::N;
+    static constexpr int chunks = (N + kChunk - 1) / kChunk;
+    static constexpr size_t tape_bytes = (size_t)N * 32 * (PAIR ? 16 : 8);
+    static constexpr size_t off_full = 2 * tape_bytes;                       // [2][chunks]
+    static constexpr size_t off_empty = off_full + 2 * (size_t)chunks * 8;   // [2]
+    static constexpr size_t bytes = off_empty + 2 * 8;
+    // resident blocks per SM: what the shared memory allows (228 KB per SM,
+    // 1 KB reserved per block), at most five (three for the paired form, whose
+    // consumers hold two families per register pair)
+    static constexpr int cap = PAIR ? 3 : 5;
+    static constexpr int per_sm =
+        (233472 / (bytes + 1024)) < cap ? (int)(233472 / (bytes + 1024)) : cap;
+};
+constexpr int kRingConsumerWarps = 8;
+template <int Q, bool PAIR>
+constexpr int ring_threads() { return 32 * ((PAIR ? 2 : 1) + kRingConsumerWarps); }
+// compiled where at least two blocks fit on an SM
+template <int Q, bool PAIR>
+constexpr bool ring_walk_compiled() { return RingSmem<Q, PAIR>::per_sm >= 2; }
+
+template <int Q, bool PAIR>
+__global__ void __launch_bounds__(ring_threads<Q, PAIR>(),
+                                  RingSmem<Q, PAIR>::per_sm < 1 ? 1 : RingSmem<Q, PAIR>::per_sm)
+    walk_ring_kernel(const WalkArgs<float> a, int64_t n_units) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    using S = RingSmem<Q, PAIR>;
+    static_assert(Q == GBN_Q, "one Q per translation unit");
+    constexpr int NP = PAIR ? 2 : 1;  // producer warps
+    constexpr int NC = kRingConsumerWarps;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::off_full);
+    uint64_t* empty = reinterpret_cast<uint64_t*>(smem + S::off_empty);
+    for (int c = threadIdx.x; c < 2 * S::chunks; c += blockDim.x) mbar_init(&full[c], NP);
+    if (threadIdx.x < 2) mbar_init(&empty[threadIdx.x], NC);
+    __syncthreads();
+    if (warp < NP) {
+        int j = 0;
+        for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x, ++j) {
+            const int s = j & 1;
+            if (j >= 2 && !warp_wait(&empty[s], ((j - 2) >> 1) & 1, a.watchdog_ns, a.status))
+                return;
+            unsigned char* tb = smem + s * S::tape_bytes;
+            uint64_t* fb = full + s * S::chunks;
+            if constexpr (PAIR) {
+                const float* rec = a.leaves + (size_t)(2 * u + warp) * a.leaf_stride;
+                if (warp == 0)
+                    produce<float, Q, 0>(a, c_steps, rec, tb, fb, lane, true);
+                else
+                    produce<float, Q, 1>(a, c_steps, rec, tb, fb, lane, true);
+            } else {
+                const float* rec = a.leaves + (size_t)u * a.leaf_stride;
+                produce<float, Q>(a, c_steps, rec, tb, fb, lane, lane < a.lanes);
+            }
+        }
+    } else {
+        const int cw = warp - NP;
+        int off = 0, j = 0;  // off: items handed out so far, mod NC
+        for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x, ++j) {
+            const int s = j & 1;
+            const unsigned par = (unsigned)(j >> 1) & 1u;
+            const int first = ((cw - off) % NC + NC) % NC;
+            const unsigned char* tb = smem + s * S::tape_bytes;
+            uint64_t* fb = full + s * S::chunks;
+            int n;
+            if constexpr (PAIR) {
+                const float* rec0 = a.leaves + (size_t)(2 * u) * a.leaf_stride;
+                n = consume_pair<Q>(a, rec0, rec0 + a.leaf_stride,
+                                    reinterpret_cast<const float4*>(tb), fb, par, lane, first, NC,
+                                    (uint64_t)u);
+            } else {
+                const float* rec = a.leaves + (size_t)u * a.leaf_stride;
+                n = consume<float, Q, false>(a, rec, reinterpret_cast<const float2*>(tb), fb, par,
+                                             lane, first, NC, (uint64_t)u, (uint64_t)u << a.W);
+            }
+            if (n < 0) return;
+            off = (off + n) % NC;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the slot
+        }
+    }
+}
+
+template <int Q, bool PAIR>
+int launch_walk_ring(const WalkArgs<float>& a, int64_t n_units, cudaStream_t stream) {
+    const size_t smem = RingSmem<Q, PAIR>::bytes;
+    const int threads = ring_threads<Q, PAIR>();
+    if (cudaFuncSetAttribute(walk_ring_kernel<Q, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return GBN_ERR_CUDA;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_ring_kernel<Q, PAIR>, threads,
+                                                      smem) != cudaSuccess)
+        return GBN_ERR_CUDA;
+    if (per_sm < 1) return GBN_ERR_CUDA;
+    const int64_t blocks = std::min<int64_t>(n_units, (int64_t)sms * per_sm);
+    walk_ring_kernel<Q, PAIR><<<(unsigned)blocks, threads, smem, stream>>>(a, n_units);
+    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+}
+
+// Which FP32 score walk a launch takes (full warps of sub-walks, W = 5):
+// 0 the per-CTA walk, 1 the paired walk, 2 the ring walk, 3 the paired ring.
+// Measured at m = 26: the paired ring is the fastest at Q = 6; at Q = 7 its
+// two tapes leave room for one block per SM and the paired walk is faster.
+template <int Q>
+constexpr int fp32_walk_form() {
+    return (Q <= 6 && ring_walk_compiled<Q, true>()) ? 3 : 1;
+}
+
 template <typename T, int Q, bool COV>
 int launch_walk_q(const WalkArgs<T>& a, int64_t n_cta, cudaStream_t stream) {
     const size_t smem = Smem<T, Q>::bytes;
     if (a.n_cwarps < 1 || a.n_cwarps > kMaxConsumerWarps) return GBN_ERR_Q;
+    if constexpr (std::is_same<T, float>::value && !COV) {
+        constexpr int form = fp32_walk_form<Q>();
+        const bool full_warps = a.W == 5 && a.lanes == 32;
+        const bool pairs = full_warps && n_cta >= 2 && n_cta % 2 == 0;
+        if constexpr (form == 3) {
+            if (pairs) return launch_walk_ring<Q, true>(a, n_cta / 2, stream);
+        }
+        if constexpr (form >= 2) {
+            if (full_warps) return launch_walk_ring<Q, false>(a, n_cta, stream);
+        }
+    }
+    if constexpr (pair_walk_compiled<T, Q, COV>()) {
+        if (fp32_walk_form<Q>() == 1 && a.W == 5 && a.lanes == 32 && n_cta >= 2 && n_cta % 2 == 0) {
+            const size_t smem_p = SmemP<Q>::bytes;
+            if (cudaFuncSetAttribute(walk_kernel_pair<Q>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_p) != cudaSuccess)
+                return GBN_ERR_CUDA;
+            walk_kernel_pair<Q><<<(unsigned)(n_cta / 2), 32 * (2 + a.n_cwarps), smem_p, stream>>>(a);
+            return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+        }
+    }
     if (cudaFuncSetAttribute(walk_kernel<T, Q, COV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return GBN_ERR_CUDA;
