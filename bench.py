@@ -479,7 +479,7 @@ def run_ours(args):
         "config": {"workload": w.name, "m": w.m, "n": w.n, "families": fam,
                    "q": q32 or binding.auto_q(w.m, 0), "precision": "fp32 walk, fp64 CholeskyQR2 R0",
                    "l2": "256 MiB buffer zeroed between timed steps (> 129 MB L2); each step "
-                         "also writes a 3.49 GB table",
+                         f"also writes a {fam * 4 / 1e9:.3g} GB table",
                    "parallelism": f"replicas x{world}, one dataset per GPU"},
         "fp64": fp64,
         "speedup_fp32_vs_fp64": (value / world) / fp64["value"] if fp64 else None,
