@@ -71,6 +71,8 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     off = align_up(off + sizeof(double) * 32, 256);
     p->off_gram = off;
     off = align_up(off + sizeof(double) * (size_t)p->panels * (m * (m + 1) / 2), 256);
+    p->off_gsum = off;
+    off = align_up(off + sizeof(double) * (size_t)(m * (m + 1) / 2), 256);
     p->off_r1 = off;
     off = align_up(off + sizeof(double) * (size_t)m * m, 256);
     p->off_r1inv = off;

@@ -221,7 +221,9 @@ extern "C" int score_all_families_batched(const double* const* Xs, const int64_t
     v.ws = reinterpret_cast<char* const*>(base + L.off_ws);
     v.out = reinterpret_cast<void* const*>(base + L.off_out);
     v.walk_args = base + L.off_args;
-    if ((rc = launch_r0_batched(v, L.total_panels, stream))) return rc;
+    int max_m = 1;
+    for (int b = 0; b < B; ++b) max_m = std::max(max_m, L.plans[b].m);
+    if ((rc = launch_r0_batched(v, L.total_panels, max_m, stream))) return rc;
     if ((rc = launch_roots_batched(v, L.total_cta, L.Q, L.maxW, L.max_stride, precision, stream))) return rc;
     return launch_walk_batched(v, L.total_cta, L.Q, precision, opts->debug_coverage != 0,
                                L.n_cwarps, stream);

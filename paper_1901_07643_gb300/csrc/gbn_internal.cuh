@@ -59,7 +59,8 @@ struct Plan {
     int center = 1;
     int coverage = 0;
     // workspace layout (byte offsets)
-    size_t off_status = 0, off_colsum = 0, off_mu = 0, off_gram = 0, off_r1 = 0, off_r1inv = 0;
+    size_t off_status = 0, off_colsum = 0, off_mu = 0, off_gram = 0, off_gsum = 0, off_r1 = 0;
+    size_t off_r1inv = 0;
     size_t off_r0 = 0;
     size_t off_leaves = 0;
     size_t off_top = 0;      // the CTA roots of the sub-walk tree (nodes at depth k - W)
@@ -140,7 +141,7 @@ __device__ __forceinline__ int batch_locate(const BatchView& v, const int64_t* p
     return v.dataset_of[lo];
 }
 
-int launch_r0_batched(const BatchView& v, int64_t total_panels, cudaStream_t stream);
+int launch_r0_batched(const BatchView& v, int64_t total_panels, int max_m, cudaStream_t stream);
 int launch_roots_batched(const BatchView& v, int64_t total_cta, int Q, int max_w,
                          size_t max_stride, int precision, cudaStream_t stream);
 int launch_walk_batched(const BatchView& v, int64_t total_cta, int Q, int precision, bool coverage,

@@ -1,7 +1,7 @@
 // Initial QR decomposition R0 of the centred data (the "initial QRD" that the
 // walk starts from, Sec. 2 and Sec. 1.3), computed as CholeskyQR2 in FP64:
 //   means:  mu = column means (per-panel partial sums, then one reduction)
-//   pass 1: G1 = Xc^T Xc (row panels, reduced), R1 = chol(G1)
+//   pass 1: G1 = Xc^T Xc (row panels, then summed over panels), R1 = chol(G1)
 //   pass 2: Q1 = Xc R1^{-1} (explicit triangular inverse), G2 = Q1^T Q1,
 //           R2 = chol(G2), R0 = R2 R1.
 // Columns are taken in the plan's order (the order the sub-walk tree decides
@@ -139,52 +139,62 @@ __device__ __forceinline__ void gram_body(int blk, const double* __restrict__ X,
         gram[(int64_t)blk * npair + tid] = acc0 + acc1;
 }
 
-// Sum the panel Grams and Cholesky-factor the sum (upper R with R^T R = G).
-// Pass 1 (R1 == nullptr): writes R1 to Rout and its inverse to Rinv_out.
-// Pass 2: the factor is R2 and R0 = R2 * R1 is written to Rout.
-// The panel sums are split over warps (lanes stride over panels, then a
-// fixed shuffle tree), the factorisation runs in one warp with one column
-// per lane, and the product uses every thread.
-__device__ __forceinline__ void chol_body(const double* __restrict__ gram, int panels, int m,
+// Sum of the panel Grams for pairs [32 g, 32 g + 32): lane l of warp w adds
+// pair 32 g + l over panels w, w + 32, ... (the loads of a warp contiguous),
+// then warp 0 adds the 32 slice sums in a fixed order.  GB300's FP64 rate is
+// low (two FMAs per clock per SM), so the sum is spread over blocks.
+__device__ __forceinline__ void gram_sum_body(int g, const double* __restrict__ gram, int panels,
+                                              int m, double* __restrict__ gsum,
+                                              unsigned long long* chk) {
+    __shared__ double part[32 * 33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int npair = m * (m + 1) / 2;
+    const int e = g * 32 + lane;
+    double a0 = 0.0, a1 = 0.0;
+    if (e < npair) {
+        int b = w;
+        for (; b + 32 < panels; b += 64) {
+            if (GBN_IN(chk, 121, (int64_t)(b + 32) * npair + e, (int64_t)panels * npair)) {
+                a0 += gram[(int64_t)b * npair + e];
+                a1 += gram[(int64_t)(b + 32) * npair + e];
+            }
+        }
+        if (b < panels && GBN_IN(chk, 122, (int64_t)b * npair + e, (int64_t)panels * npair))
+            a0 += gram[(int64_t)b * npair + e];
+    }
+    part[w * 33 + lane] = a0 + a1;
+    __syncthreads();
+    if (w == 0 && e < npair) {
+        double acc = 0.0;
+        for (int k = 0; k < 32; ++k) acc += part[k * 33 + lane];
+        gsum[e] = acc;
+    }
+}
+
+// Cholesky-factor the summed Gram (upper R with R^T R = G, pairs packed by
+// rows).  Pass 1 (R1 == nullptr): writes R1 to Rout and its inverse to
+// Rinv_out.  Pass 2: the factor is R2 and R0 = R2 * R1 is written to Rout.
+// Both the factorisation and the inverse are right-looking with one barrier
+// per column: the threads of the row that a step completes scale it at once
+// (each forms the pivot's 1/sqrt itself from values nobody writes in that
+// step), so the next step reads it final.  The operations and their order
+// per element are those of the textbook right-looking forms.
+__device__ __forceinline__ void chol_body(const double* __restrict__ gsum, int m,
                                           const double* __restrict__ R1, double* __restrict__ Rout,
                                           double* __restrict__ Rinv_out, int* __restrict__ status,
                                           unsigned long long* chk) {
     __shared__ double G[32 * kLd];
     __shared__ double R1s[32 * kLd];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nwarps = kRedThreads / 32;
-    const int npair = m * (m + 1) / 2;
-    for (int e = tid; e < 32 * kLd; e += blockDim.x) G[e] = 0.0;
-    if (R1)
-        for (int e = tid; e < m * m; e += blockDim.x) R1s[(e / m) * kLd + e % m] = R1[e];
-    __syncthreads();
-    for (int e = warp; e < npair; e += nwarps) {
-        double s0 = 0.0, s1 = 0.0;
-        int b = lane;
-        for (; b + 32 < panels; b += 64) {
-            if (GBN_IN(chk, 121, (int64_t)(b + 32) * npair + e, (int64_t)panels * npair)) {
-                s0 += gram[(int64_t)b * npair + e];
-                s1 += gram[(int64_t)(b + 32) * npair + e];
-            }
-        }
-        if (b < panels && GBN_IN(chk, 122, (int64_t)b * npair + e, (int64_t)panels * npair))
-            s0 += gram[(int64_t)b * npair + e];
-        double s = s0 + s1;
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-            int q = e, i = 0;
-            while (q >= m - i) {
-                q -= m - i;
-                ++i;
-            }
-            if (GBN_IN(chk, 123, i * kLd + i + q, 32 * kLd)) G[i * kLd + i + q] = s;
-        }
-    }
     // pair table: pairs (a, b), a <= b, ordered by a, so that the pairs with
     // a > j are a suffix starting at pair_start[j + 1]
     __shared__ short2 pairs[32 * 33 / 2 + 1];
     __shared__ int pair_start[33];
-    __shared__ double dinv[32];
+    __shared__ double dinv[32], diag[32];
+    const int tid = threadIdx.x;
+    const int npair = m * (m + 1) / 2;
+    for (int e = tid; e < 32 * kLd; e += blockDim.x) G[e] = 0.0;
+    if (R1)
+        for (int e = tid; e < m * m; e += blockDim.x) R1s[(e / m) * kLd + e % m] = R1[e];
     if (tid <= m) {
         int st = 0;
         for (int a = 0; a < tid; ++a) st += m - a;
@@ -199,42 +209,59 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ gram, int p
         pairs[e] = make_short2((short)a, (short)(a + q));
     }
     __syncthreads();
-    // right-looking Cholesky over all threads: per column one reciprocal
-    // square root, the row scaled by it, then every trailing pair updated once
-    for (int j = 0; j < m; ++j) {
-        if (tid == 0) {
-            const double d = G[j * kLd + j];
-            const double inv = d > 0.0 ? rsqrt(d) : 0.0;
-            if (!(d > 0.0)) atomicOr(status, GBN_STATUS_RANK_DEFICIENT);
-            dinv[j] = inv;
-            G[j * kLd + j] = d * inv;
-        }
-        __syncthreads();
-        const double inv = dinv[j];
-        for (int l = j + 1 + tid; l < m; l += blockDim.x) G[j * kLd + l] *= inv;
-        __syncthreads();
-        for (int e = pair_start[j + 1] + tid; e < npair; e += blockDim.x) {
+    for (int e = tid; e < npair; e += blockDim.x) {
+        const short2 ab = pairs[e];
+        if (GBN_IN(chk, 123, ab.x * kLd + ab.y, 32 * kLd)) G[ab.x * kLd + ab.y] = gsum[e];
+    }
+    __syncthreads();
+    // Cholesky.  Step j (-1 .. m-2) completes row j+1: its owners take the
+    // pivot d = G_{j+1,j+1} - r_{j,j+1}^2 (the diagonal is never written
+    // during a step: the scaled diagonal goes to diag[]) and scale by 1/sqrt(d).
+    for (int j = -1; j < m - 1; ++j) {
+        const int r = j + 1;  // the row this step completes
+        for (int e = pair_start[r] + tid; e < npair; e += blockDim.x) {
             const short2 ab = pairs[e];
-            G[ab.x * kLd + ab.y] -= G[j * kLd + ab.x] * G[j * kLd + ab.y];
+            double v = G[ab.x * kLd + ab.y];
+            if (j >= 0) v -= G[j * kLd + ab.x] * G[j * kLd + ab.y];
+            if (ab.x == r) {
+                double d = G[r * kLd + r];
+                if (j >= 0) d -= G[j * kLd + r] * G[j * kLd + r];
+                const double inv = d > 0.0 ? rsqrt(d) : 0.0;
+                if (ab.y == r) {
+                    if (!(d > 0.0)) atomicOr(status, GBN_STATUS_RANK_DEFICIENT);
+                    dinv[r] = inv;
+                    diag[r] = d * inv;
+                } else {
+                    G[ab.x * kLd + ab.y] = v * inv;
+                }
+            } else {
+                G[ab.x * kLd + ab.y] = v;
+            }
         }
         __syncthreads();
     }
+    for (int r = tid; r < m; r += blockDim.x) G[r * kLd + r] = diag[r];
+    __syncthreads();
     if (!R1 && Rinv_out) {
-        // R^{-1} right-looking from the last row: row j of X = B[j] / R_jj,
-        // then rows i < j of B lose R_ij * X[j] (B starts as I); zero pivots
-        // give zero rows
+        // R^{-1} = B right-looking from the last row: row j of B is B_j / R_jj,
+        // then rows i < j lose R_ij * (row j).  Step j updates columns c >= j
+        // of rows i < j and completes row j - 1 (scaled by 1/R_{j-1,j-1}).
         double* B = R1s;  // unused in this pass
         for (int e = tid; e < 32 * kLd; e += blockDim.x) B[e] = 0.0;
         __syncthreads();
-        for (int e = tid; e < m; e += blockDim.x) B[e * kLd + e] = 1.0;
+        for (int e = tid; e < m; e += blockDim.x) B[e * kLd + e] = (e == m - 1) ? dinv[e] : 1.0;
         __syncthreads();
-        for (int j = m - 1; j >= 0; --j) {
-            for (int c = j + tid; c < m; c += blockDim.x) B[j * kLd + c] *= dinv[j];
-            __syncthreads();
+        for (int j = m - 1; j >= 1; --j) {
             const int w = m - j;  // columns j .. m-1
-            for (int e = tid; e < j * w; e += blockDim.x) {
+            for (int e = tid; e <= j * w; e += blockDim.x) {
+                if (e == j * w) {  // the diagonal of the completed row
+                    B[(j - 1) * kLd + (j - 1)] = dinv[j - 1];
+                    continue;
+                }
                 const int i = e / w, c = j + e % w;
-                B[i * kLd + c] -= G[i * kLd + j] * B[j * kLd + c];
+                double v = B[i * kLd + c] - G[i * kLd + j] * B[j * kLd + c];
+                if (i == j - 1) v *= dinv[j - 1];
+                B[i * kLd + c] = v;
             }
             __syncthreads();
         }
@@ -260,7 +287,7 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ gram, int p
 
 // Stage pointers of one dataset inside its workspace region.
 struct R0Ptrs {
-    double *colsum, *mu, *gram, *r1, *r1inv, *r0;
+    double *colsum, *mu, *gram, *gsum, *r1, *r1inv, *r0;
     int* status;
     unsigned long long* chk;
 };
@@ -270,6 +297,7 @@ __device__ __host__ __forceinline__ R0Ptrs r0_ptrs(const Plan& p, char* ws) {
     q.colsum = reinterpret_cast<double*>(ws + p.off_colsum);
     q.mu = reinterpret_cast<double*>(ws + p.off_mu);
     q.gram = reinterpret_cast<double*>(ws + p.off_gram);
+    q.gsum = reinterpret_cast<double*>(ws + p.off_gsum);
     q.r1 = reinterpret_cast<double*>(ws + p.off_r1);
     q.r1inv = reinterpret_cast<double*>(ws + p.off_r1inv);
     q.r0 = reinterpret_cast<double*>(ws + p.off_r0);
@@ -292,12 +320,16 @@ __global__ void gram_kernel(const Plan p, const double* __restrict__ X, char* ws
     gram_body(blockIdx.x, X, p.n, p.m, p.rows_per_panel, q.mu, p.panels, pass ? q.r1inv : nullptr,
               p, q.gram, q.chk);
 }
+__global__ void __launch_bounds__(kRedThreads) gram_sum_kernel(const Plan p, char* ws) {
+    const R0Ptrs q = r0_ptrs(p, ws);
+    gram_sum_body(blockIdx.x, q.gram, p.panels, p.m, q.gsum, q.chk);
+}
 __global__ void __launch_bounds__(kRedThreads) chol_kernel(const Plan p, char* ws, int pass) {
     const R0Ptrs q = r0_ptrs(p, ws);
     if (pass)
-        chol_body(q.gram, p.panels, p.m, q.r1, q.r0, nullptr, q.status, q.chk);
+        chol_body(q.gsum, p.m, q.r1, q.r0, nullptr, q.status, q.chk);
     else
-        chol_body(q.gram, p.panels, p.m, nullptr, q.r1, q.r1inv, q.status, q.chk);
+        chol_body(q.gsum, p.m, nullptr, q.r1, q.r1inv, q.status, q.chk);
 }
 
 // A batch: blocks are mapped to (dataset, panel) through the prefix of panels.
@@ -328,14 +360,22 @@ __global__ void gram_kernel_b(const BatchView v, int pass) {
     gram_body((int)local, v.X[d], p.n, p.m, p.rows_per_panel, q.mu, p.panels,
               pass ? q.r1inv : nullptr, p, q.gram, q.chk);
 }
+// grid (pair groups of the largest m, datasets)
+__global__ void __launch_bounds__(kRedThreads) gram_sum_kernel_b(const BatchView v) {
+    const int d = blockIdx.y;
+    const Plan& p = v.plans[d];
+    if ((int)blockIdx.x * 32 >= p.m * (p.m + 1) / 2) return;
+    const R0Ptrs q = r0_ptrs(p, v.ws[d]);
+    gram_sum_body(blockIdx.x, q.gram, p.panels, p.m, q.gsum, q.chk);
+}
 __global__ void __launch_bounds__(kRedThreads) chol_kernel_b(const BatchView v, int pass) {
     const int d = blockIdx.x;
     const Plan& p = v.plans[d];
     const R0Ptrs q = r0_ptrs(p, v.ws[d]);
     if (pass)
-        chol_body(q.gram, p.panels, p.m, q.r1, q.r0, nullptr, q.status, q.chk);
+        chol_body(q.gsum, p.m, q.r1, q.r0, nullptr, q.status, q.chk);
     else
-        chol_body(q.gram, p.panels, p.m, nullptr, q.r1, q.r1inv, q.status, q.chk);
+        chol_body(q.gsum, p.m, nullptr, q.r1, q.r1inv, q.status, q.chk);
 }
 
 }  // namespace
@@ -344,21 +384,27 @@ int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream) {
     if (cudaMemsetAsync(ws + p.off_status, 0, 256, stream) != cudaSuccess) return GBN_ERR_CUDA;
     if (p.center) colsum_kernel<<<p.panels, 256, 0, stream>>>(p, X, ws);
     mean_kernel<<<1, kRedThreads, 0, stream>>>(p, ws);
+    const unsigned groups = (unsigned)((p.m * (p.m + 1) / 2 + 31) / 32);
     gram_kernel<<<p.panels, 512, 0, stream>>>(p, X, ws, 0);
+    gram_sum_kernel<<<groups, kRedThreads, 0, stream>>>(p, ws);
     chol_kernel<<<1, kRedThreads, 0, stream>>>(p, ws, 0);
     gram_kernel<<<p.panels, 512, 0, stream>>>(p, X, ws, 1);
+    gram_sum_kernel<<<groups, kRedThreads, 0, stream>>>(p, ws);
     chol_kernel<<<1, kRedThreads, 0, stream>>>(p, ws, 1);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
-int launch_r0_batched(const BatchView& v, int64_t total_panels, cudaStream_t stream) {
+int launch_r0_batched(const BatchView& v, int64_t total_panels, int max_m, cudaStream_t stream) {
     const unsigned B = (unsigned)v.B, P = (unsigned)total_panels;
     status_clear_kernel_b<<<B, 64, 0, stream>>>(v);
     colsum_kernel_b<<<P, 256, 0, stream>>>(v);
     mean_kernel_b<<<B, kRedThreads, 0, stream>>>(v);
+    const dim3 sum_grid((unsigned)((max_m * (max_m + 1) / 2 + 31) / 32), B);
     gram_kernel_b<<<P, 512, 0, stream>>>(v, 0);
+    gram_sum_kernel_b<<<sum_grid, kRedThreads, 0, stream>>>(v);
     chol_kernel_b<<<B, kRedThreads, 0, stream>>>(v, 0);
     gram_kernel_b<<<P, 512, 0, stream>>>(v, 1);
+    gram_sum_kernel_b<<<sum_grid, kRedThreads, 0, stream>>>(v);
     chol_kernel_b<<<B, kRedThreads, 0, stream>>>(v, 1);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
