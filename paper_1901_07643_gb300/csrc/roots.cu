@@ -21,11 +21,12 @@
 // lane's role (undecided / in F / carried in B) and drops one row.
 //
 // Two kernels, each with a small instruction footprint:
-//   * top: one warp per walk CTA follows the CTA's path through the k - W top
-//     levels on a node kept in shared memory (rows addressed through a moving
-//     first-row offset, a compact loop per rotation) and stores the node it
-//     reaches: the Q + W live rows of every column, the residuals and the
-//     carried-column mask;
+//   * top: one warp per 16 walk CTAs follows their shared path through the
+//     top levels and enumerates their last 4 top levels depth first, on a
+//     node kept in shared memory (rows addressed through a moving first-row
+//     offset, a compact loop per rotation), storing each CTA's node: the Q + W
+//     live rows of every column, the residuals and the carried-column mask
+//     (the batched form takes one CTA per warp);
 //   * leaves: one warp per walk CTA loads that node into registers (at most
 //     16 rows) and enumerates the 2^W leaves of the last W levels depth first,
 //     saving each level's node in shared memory to restart from it, and
@@ -40,7 +41,7 @@ namespace gbn {
 namespace {
 
 constexpr int kDfsRows = 16;  // register rows of the depth-first nodes (Q + W <= 16)
-constexpr int kTopWarps = 4;  // warps per block of the top kernel (one CTA root each)
+constexpr int kTopWarps = 4;  // warps per block of the batched top kernel (one CTA root each)
 constexpr int kDfsWarps = 4;  // warps per block of the leaf kernel (one walk CTA each)
 
 // Compile-time loop: f(integral_constant<int, i>) for i in the sequence, so
@@ -83,46 +84,140 @@ __device__ __forceinline__ int var_of_lane(const Plan& p, int lane) {
 
 // ------------------------------------------------------------- top levels
 
+// A node in shared memory: live rows r0 .. r0 + rows - 1 of S (row r of the
+// lane's column at S[r * 32 + lane]), the carried residuals and mask.
 template <typename T>
-__device__ __forceinline__ void top_body(const double* __restrict__ R0, const Plan& p,
-                                         T* __restrict__ top, unsigned long long* chk,
-                                         uint64_t cta, T* S /* 32 x 32, [row * 32 + lane] */) {
+struct TopNode {
+    int r0, rows;
+    T C;
+    unsigned carried;
+};
+
+template <typename T>
+__device__ __forceinline__ void top_load(const double* __restrict__ R0, const Plan& p,
+                                         unsigned long long* chk, T* S, TopNode<T>& nd) {
     const int lane = threadIdx.x & 31, m = p.m;
     for (int r = 0; r < 32; ++r)
         S[r * 32 + lane] = (r < m && lane < m && GBN_IN(chk, 231, r * m + lane, m * m))
                                ? (T)R0[r * m + lane]
                                : T(0);
     __syncwarp();
-    T C = T(0);
-    unsigned carried = 0u;
-    int r0 = 0, rows = m;  // live rows r0 .. r0 + rows - 1
-    for (int f = 0; f < p.k - p.W; ++f) {
-        if ((cta >> f) & 1ull) {  // include: the first live row goes
-            ++r0;
-            --rows;
-            continue;
-        }
-        carried |= 1u << f;  // exclude: column f leaves the triangle
-        for (int j = 0; j + 1 < rows; ++j) {
-            const int ra = r0 + j, piv = f + 1 + j;
-            const T a = S[ra * 32 + piv], b = S[(ra + 1) * 32 + piv];
-            const T x = S[ra * 32 + lane], y = S[(ra + 1) * 32 + lane];
-            T c, s;
-            givens_cs(a, b, c, s);
-            __syncwarp();
-            S[ra * 32 + lane] = fma(c, x, s * y);
-            S[(ra + 1) * 32 + lane] = fma(c, y, -s * x);
-            __syncwarp();
-        }
-        const T yb = S[(r0 + rows - 1) * 32 + lane];  // the bottom row falls off
-        if ((carried >> lane) & 1u) C = fma(yb, yb, C);
-        --rows;
+    nd.r0 = 0;
+    nd.rows = m;
+    nd.C = T(0);
+    nd.carried = 0u;
+}
+
+// Decide fixed variable f (the node's first live column): include drops the
+// first live row; exclude carries column f and re-triangularises the rest.
+template <typename T>
+__device__ __forceinline__ void top_decide(T* S, TopNode<T>& nd, int f, bool include) {
+    const int lane = threadIdx.x & 31;
+    if (include) {
+        ++nd.r0;
+        --nd.rows;
+        return;
     }
-    // rows == Q + W: store the node
-    T* out = top + (size_t)cta * node_elems(rows);
-    for (int r = 0; r < rows; ++r) out[(size_t)r * 32 + lane] = S[(r0 + r) * 32 + lane];
-    out[(size_t)rows * 32 + lane] = C;
-    if (lane == 0) *mask_of(out, rows) = carried;
+    nd.carried |= 1u << f;
+    for (int j = 0; j + 1 < nd.rows; ++j) {
+        const int ra = nd.r0 + j, piv = f + 1 + j;
+        const T a = S[ra * 32 + piv], b = S[(ra + 1) * 32 + piv];
+        const T x = S[ra * 32 + lane], y = S[(ra + 1) * 32 + lane];
+        T c, s;
+        givens_cs(a, b, c, s);
+        __syncwarp();
+        S[ra * 32 + lane] = fma(c, x, s * y);
+        S[(ra + 1) * 32 + lane] = fma(c, y, -s * x);
+        __syncwarp();
+    }
+    const T yb = S[(nd.r0 + nd.rows - 1) * 32 + lane];  // the bottom row falls off
+    if ((nd.carried >> lane) & 1u) nd.C = fma(yb, yb, nd.C);
+    --nd.rows;
+}
+
+// rows == Q + W: store the node as walk CTA cta's root
+template <typename T>
+__device__ __forceinline__ void top_store(const T* S, const TopNode<T>& nd, T* __restrict__ top,
+                                          uint64_t cta) {
+    const int lane = threadIdx.x & 31;
+    T* out = top + (size_t)cta * node_elems(nd.rows);
+    for (int r = 0; r < nd.rows; ++r) out[(size_t)r * 32 + lane] = S[(nd.r0 + r) * 32 + lane];
+    out[(size_t)nd.rows * 32 + lane] = nd.C;
+    if (lane == 0) *mask_of(out, nd.rows) = nd.carried;
+}
+
+// One walk CTA's root: its path through the k - W top levels.
+template <typename T>
+__device__ __forceinline__ void top_body(const double* __restrict__ R0, const Plan& p,
+                                         T* __restrict__ top, unsigned long long* chk,
+                                         uint64_t cta, T* S /* 32 x 32, [row * 32 + lane] */) {
+    TopNode<T> nd;
+    top_load(R0, p, chk, S, nd);
+    for (int f = 0; f < p.k - p.W; ++f) top_decide(S, nd, f, ((cta >> f) & 1ull) != 0);
+    top_store(S, nd, top, cta);
+}
+
+// The roots of 2^d walk CTAs at once: they share the path through the first
+// P = k - W - d top levels (the low P bits of the CTA index) and differ in
+// the last d, which one warp enumerates depth first, so every node of the
+// subtree is built once (a path per CTA builds the shared part 2^d times).
+// Level t's node is saved in its stack slot before the include branch and
+// restored for the exclude branch; the results are bit-identical to top_body.
+constexpr int kTopDfsLevels = 4;
+constexpr int kTopDfsWarps = 2;
+
+template <typename T, int L>
+struct TopDfs {
+    __device__ static __forceinline__ void run(T* S, T* stack, const TopNode<T>& nd, int f,
+                                               int nlev, uint64_t cta, T* __restrict__ top) {
+        if constexpr (L < kTopDfsLevels) {
+            if (L < nlev) {
+                const int lane = threadIdx.x & 31;
+                T* slot = stack;  // this level's slot; deeper levels follow it
+                for (int r = 0; r < nd.rows; ++r) slot[r * 32 + lane] = S[(nd.r0 + r) * 32 + lane];
+                __syncwarp();
+                T* deeper = stack + (size_t)nd.rows * 32;
+                TopNode<T> c = nd;
+                top_decide(S, c, f, true);
+                TopDfs<T, L + 1>::run(S, deeper, c, f + 1, nlev, cta | (1ull << f), top);
+                __syncwarp();
+                for (int r = 0; r < nd.rows; ++r) S[(nd.r0 + r) * 32 + lane] = slot[r * 32 + lane];
+                __syncwarp();
+                c = nd;
+                top_decide(S, c, f, false);
+                TopDfs<T, L + 1>::run(S, deeper, c, f + 1, nlev, cta, top);
+                return;
+            }
+        }
+        top_store(S, nd, top, cta);
+        __syncwarp();
+    }
+};
+
+// Levels enumerated depth first by one top warp, and the stack it needs
+// (elements: each level's saved rows).
+__host__ __device__ __forceinline__ int top_dfs_levels(const Plan& p) {
+    const int D = p.k - p.W;
+    return D < kTopDfsLevels ? D : kTopDfsLevels;
+}
+__host__ __device__ __forceinline__ size_t top_dfs_stack_elems(const Plan& p) {
+    const int nlev = top_dfs_levels(p);
+    const int rows0 = p.m - (p.k - p.W - nlev);  // live rows when the subtree starts
+    size_t e = 0;
+    for (int t = 0; t < nlev; ++t) e += (size_t)(rows0 - t) * 32;
+    return e;
+}
+
+template <typename T>
+__device__ __forceinline__ void top_dfs_body(const double* __restrict__ R0, const Plan& p,
+                                             T* __restrict__ top, unsigned long long* chk,
+                                             uint64_t g, T* S, T* stack) {
+    const int nlev = top_dfs_levels(p);
+    const int P = p.k - p.W - nlev;
+    TopNode<T> nd;
+    top_load(R0, p, chk, S, nd);
+    for (int f = 0; f < P; ++f) top_decide(S, nd, f, ((g >> f) & 1ull) != 0);
+    TopDfs<T, 0>::run(S, stack, nd, P, nlev, g, top);
 }
 
 // ------------------------------------------------------------- last W levels
@@ -460,15 +555,19 @@ __device__ __forceinline__ T* top_nodes(const Plan& p, char* ws) {
     return reinterpret_cast<T*>(ws + p.off_top);
 }
 
+
+// One warp per group of 2^d walk CTAs (the low P bits of the CTA index).
 template <typename T>
-__global__ void __launch_bounds__(32 * kTopWarps) roots_top_kernel(const Plan p, char* ws) {
-    __shared__ T S[kTopWarps * 32 * 32];
+__global__ void __launch_bounds__(32 * kTopDfsWarps) roots_top_dfs_kernel(const Plan p, char* ws) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
-    const uint64_t cta = (uint64_t)blockIdx.x * kTopWarps + warp;
-    if (cta >= (uint64_t)p.n_cta) return;
-    top_body<T>(reinterpret_cast<const double*>(ws + p.off_r0), p, top_nodes<T>(p, ws),
-                reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset), cta,
-                S + warp * 32 * 32);
+    const uint64_t g = (uint64_t)blockIdx.x * kTopDfsWarps + warp;
+    const uint64_t groups = (uint64_t)p.n_cta >> top_dfs_levels(p);
+    if (g >= groups) return;
+    T* base = reinterpret_cast<T*>(smem_raw) + (size_t)warp * (32 * 32 + top_dfs_stack_elems(p));
+    top_dfs_body<T>(reinterpret_cast<const double*>(ws + p.off_r0), p, top_nodes<T>(p, ws),
+                    reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset), g, base,
+                    base + 32 * 32);
 }
 
 template <typename T>
@@ -535,9 +634,14 @@ int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
     const size_t smem = sizeof(T) * warp_smem_elems(p.Q, p.W, p.leaf_stride) * kDfsWarps;
     if (smem > 227 * 1024) return GBN_ERR_Q;
     if (roots_attr<T>(smem)) return GBN_ERR_CUDA;
-    const unsigned nb_top = (unsigned)((p.n_cta + kTopWarps - 1) / kTopWarps);
+    const uint64_t groups = (uint64_t)p.n_cta >> top_dfs_levels(p);
+    const unsigned nb_top = (unsigned)((groups + kTopDfsWarps - 1) / kTopDfsWarps);
+    const size_t smem_top = sizeof(T) * (32 * 32 + top_dfs_stack_elems(p)) * kTopDfsWarps;
+    if (cudaFuncSetAttribute(roots_top_dfs_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_top) != cudaSuccess)
+        return GBN_ERR_CUDA;
     const unsigned nb_dfs = (unsigned)((p.n_cta + kDfsWarps - 1) / kDfsWarps);
-    roots_top_kernel<T><<<nb_top, 32 * kTopWarps, 0, stream>>>(p, ws);
+    roots_top_dfs_kernel<T><<<nb_top, 32 * kTopDfsWarps, smem_top, stream>>>(p, ws);
     roots_leaves_kernel<T><<<nb_dfs, 32 * kDfsWarps, smem, stream>>>(p, ws);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
