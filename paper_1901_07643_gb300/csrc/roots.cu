@@ -21,8 +21,8 @@
 // lane's role (undecided / in F / carried in B) and drops one row.
 //
 // Two kernels, each with a small instruction footprint:
-//   * top: one warp per 16 walk CTAs follows their shared path through the
-//     top levels and enumerates their last 4 top levels depth first, on a
+//   * top: one warp per 4 walk CTAs follows their shared path through the
+//     top levels and enumerates their last 2 top levels depth first, on a
 //     node kept in shared memory (rows addressed through a moving first-row
 //     offset, a compact loop per rotation), storing each CTA's node: the Q + W
 //     live rows of every column, the residuals and the carried-column mask
@@ -33,6 +33,7 @@
 //     writes every leaf, lane-interleaved, into the record the walk reads.
 #include <math.h>
 
+#include <type_traits>
 #include <utility>
 
 #include "gbn_internal.cuh"
@@ -163,7 +164,10 @@ __device__ __forceinline__ void top_body(const double* __restrict__ R0, const Pl
 // subtree is built once (a path per CTA builds the shared part 2^d times).
 // Level t's node is saved in its stack slot before the include branch and
 // restored for the exclude branch; the results are bit-identical to top_body.
-constexpr int kTopDfsLevels = 4;
+// The chains of rotations are latency-bound, so d trades work for parallel
+// warps: at m = 26 the kernel took 85.5 us with d = 0, 43.7 us with d = 2 and
+// 72.7 us with d = 4.
+constexpr int kTopDfsLevels = 2;
 constexpr int kTopDfsWarps = 2;
 
 template <typename T, int L>
@@ -519,7 +523,79 @@ struct Dfs5 {
     }
 };
 
-template <typename T, int Q>
+// FP32 form of the same enumeration with the saved nodes in registers (one
+// array per level, constant indices): a level's node is copied before the
+// include branch and copied back for the exclude branch, with no shared
+// memory traffic, and shared memory holds only the leaf staging.  In the
+// exclude, the pivot lane forms each rotation from its own column (row j as
+// rotated so far, row j+1 untouched) and broadcasts it: the same (c, s) every
+// lane formed from the shuffled and the saved entry before.
+template <typename T, int RT, int rows>
+__device__ __forceinline__ void exclude_r(T (&M)[RT], T& C, int front, bool carried) {
+    sfor(std::make_integer_sequence<int, rows - 1>{}, [&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        const int piv = front + 1 + j;
+        T c, s;
+        givens_cs(M[j], M[j + 1], c, s);
+        c = __shfl_sync(0xffffffffu, c, piv);
+        s = __shfl_sync(0xffffffffu, s, piv);
+        const T x = M[j], y = M[j + 1];
+        M[j] = fma(c, x, s * y);
+        M[j + 1] = fma(c, y, -s * x);
+    });
+    if (carried) C = fma(M[rows - 1], M[rows - 1], C);
+    M[rows - 1] = T(0);
+}
+
+template <typename T, int Q, int L>
+struct Dfs5R {
+    static constexpr int W = 5, RT = Q + W, rows = RT - L;
+    __device__ static __forceinline__ void run(T (&M)[RT], T& C, unsigned& carried, int lane,
+                                               int topk, int ell, T* stg, const Plan& p, T* rec,
+                                               unsigned long long* chk) {
+        if constexpr (L == W) {
+            stage_leaf_q<T, Q, RT>(M, C, p, lane, carried, ell, stg, rec, chk);
+        } else {
+            T sv[rows];
+            sfor(std::make_integer_sequence<int, rows>{}, [&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                sv[r] = M[r];
+            });
+            const T svC = C;
+            const unsigned svK = carried;
+#pragma unroll 1
+            for (int b = 1; b >= 0; --b) {
+                if (b) {
+                    include_n<T, RT, rows>(M);
+                } else {
+                    sfor(std::make_integer_sequence<int, rows>{}, [&](auto rc) {
+                        constexpr int r = decltype(rc)::value;
+                        M[r] = sv[r];
+                    });
+                    C = svC;
+                    carried = svK | (1u << (topk + L));
+                    exclude_r<T, RT, rows>(M, C, topk + L, (carried >> lane) & 1u);
+                }
+                Dfs5R<T, Q, L + 1>::run(M, C, carried, lane, topk, ell | (b << (W - 1 - L)), stg,
+                                        p, rec, chk);
+            }
+        }
+    }
+};
+
+// Whether the leaf kernel keeps its depth-first stack in registers (FP32,
+// W = 5, a compiled Q): its shared memory is then the leaf staging alone.
+template <typename T>
+__host__ __device__ __forceinline__ bool leaves_in_registers(int Q, int W) {
+    return std::is_same<T, float>::value && W == 5 && Q >= 4 && Q <= 9;
+}
+template <typename T>
+__host__ __device__ __forceinline__ size_t leaf_warp_elems(const Plan& p) {
+    return leaves_in_registers<T>(p.Q, p.W) ? (p.leaf_stride / 32) * 8
+                                              : warp_smem_elems(p.Q, p.W, p.leaf_stride);
+}
+
+template <typename T, int Q, bool REG>
 __device__ __forceinline__ void leaves_w5(const T* __restrict__ top, const Plan& p,
                                           T* __restrict__ leaves, unsigned long long* chk,
                                           uint64_t cta, T* stack) {
@@ -529,23 +605,28 @@ __device__ __forceinline__ void leaves_w5(const T* __restrict__ top, const Plan&
     T C;
     unsigned carried;
     load_n<T, RT, RT>(top + (size_t)cta * node_elems(RT), M, C, carried, lane);
-    Dfs5<T, Q, 0>::run(M, C, carried, lane, p.k - 5, 0, stack, p, leaves + (size_t)cta * p.leaf_stride,
-                       chk);
+    if constexpr (REG)  // staging at the start of the warp's shared memory
+        Dfs5R<T, Q, 0>::run(M, C, carried, lane, p.k - 5, 0, stack, p,
+                            leaves + (size_t)cta * p.leaf_stride, chk);
+    else
+        Dfs5<T, Q, 0>::run(M, C, carried, lane, p.k - 5, 0, stack, p,
+                           leaves + (size_t)cta * p.leaf_stride, chk);
 }
 
-// The specialised enumeration when W = 5 and Q is one of the compiled sizes.
+// The specialised enumeration (shared-memory stack) when W = 5 and Q is one
+// of the compiled sizes; the batched leaf kernel's dispatch.
 template <typename T>
 __device__ __forceinline__ bool leaves_fast(const T* __restrict__ top, const Plan& p,
                                             T* __restrict__ leaves, unsigned long long* chk,
                                             uint64_t cta, T* stack) {
     if (p.W != 5) return false;
     switch (p.Q) {
-        case 4: leaves_w5<T, 4>(top, p, leaves, chk, cta, stack); return true;
-        case 5: leaves_w5<T, 5>(top, p, leaves, chk, cta, stack); return true;
-        case 6: leaves_w5<T, 6>(top, p, leaves, chk, cta, stack); return true;
-        case 7: leaves_w5<T, 7>(top, p, leaves, chk, cta, stack); return true;
-        case 8: leaves_w5<T, 8>(top, p, leaves, chk, cta, stack); return true;
-        case 9: leaves_w5<T, 9>(top, p, leaves, chk, cta, stack); return true;
+        case 4: leaves_w5<T, 4, false>(top, p, leaves, chk, cta, stack); return true;
+        case 5: leaves_w5<T, 5, false>(top, p, leaves, chk, cta, stack); return true;
+        case 6: leaves_w5<T, 6, false>(top, p, leaves, chk, cta, stack); return true;
+        case 7: leaves_w5<T, 7, false>(top, p, leaves, chk, cta, stack); return true;
+        case 8: leaves_w5<T, 8, false>(top, p, leaves, chk, cta, stack); return true;
+        case 9: leaves_w5<T, 9, false>(top, p, leaves, chk, cta, stack); return true;
         default: return false;
     }
 }
@@ -570,16 +651,22 @@ __global__ void __launch_bounds__(32 * kTopDfsWarps) roots_top_dfs_kernel(const 
                     base + 32 * 32);
 }
 
-template <typename T>
+// One dataset: QF = the compiled Q of the specialised enumeration (FP32
+// with the stack in registers, FP64 in shared memory), or 0 for the generic
+// one; each instance gets the registers its own Q needs.
+template <typename T, int QF>
 __global__ void __launch_bounds__(32 * kDfsWarps) roots_leaves_kernel(const Plan p, char* ws) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
     const uint64_t cta = (uint64_t)blockIdx.x * kDfsWarps + warp;
     if (cta >= (uint64_t)p.n_cta) return;
-    T* stack = reinterpret_cast<T*>(smem_raw) + warp * warp_smem_elems(p.Q, p.W, p.leaf_stride);
+    T* stack = reinterpret_cast<T*>(smem_raw) + warp * leaf_warp_elems<T>(p);
     T* leaves = reinterpret_cast<T*>(ws + p.off_leaves);
     unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
-    if (!leaves_fast<T>(top_nodes<T>(p, ws), p, leaves, chk, cta, stack))
+    if constexpr (QF > 0)
+        leaves_w5<T, QF, std::is_same<T, float>::value>(top_nodes<T>(p, ws), p, leaves, chk, cta,
+                                                         stack);
+    else
         leaves_body<T>(top_nodes<T>(p, ws), p, leaves, chk, cta, stack);
 }
 
@@ -618,31 +705,39 @@ __global__ void __launch_bounds__(32 * kDfsWarps) roots_leaves_kernel_b(const Ba
         leaves_body<T>(top_nodes<T>(p, ws), p, leaves, chk, (uint64_t)local, stack);
 }
 
-template <typename T>
-int roots_attr(size_t smem) {
-    if (cudaFuncSetAttribute(roots_leaves_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(roots_leaves_kernel_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <typename T, int QF>
+int launch_leaves_q(const Plan& p, char* ws, size_t smem, cudaStream_t stream) {
+    if (cudaFuncSetAttribute(roots_leaves_kernel<T, QF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return GBN_ERR_CUDA;
+    const unsigned nb = (unsigned)((p.n_cta + kDfsWarps - 1) / kDfsWarps);
+    roots_leaves_kernel<T, QF><<<nb, 32 * kDfsWarps, smem, stream>>>(p, ws);
     return GBN_OK;
 }
 
 template <typename T>
 int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
     if (p.Q + p.W > kDfsRows) return GBN_ERR_Q;
-    const size_t smem = sizeof(T) * warp_smem_elems(p.Q, p.W, p.leaf_stride) * kDfsWarps;
+    const size_t smem = sizeof(T) * leaf_warp_elems<T>(p) * kDfsWarps;
     if (smem > 227 * 1024) return GBN_ERR_Q;
-    if (roots_attr<T>(smem)) return GBN_ERR_CUDA;
     const uint64_t groups = (uint64_t)p.n_cta >> top_dfs_levels(p);
     const unsigned nb_top = (unsigned)((groups + kTopDfsWarps - 1) / kTopDfsWarps);
     const size_t smem_top = sizeof(T) * (32 * 32 + top_dfs_stack_elems(p)) * kTopDfsWarps;
     if (cudaFuncSetAttribute(roots_top_dfs_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_top) != cudaSuccess)
         return GBN_ERR_CUDA;
-    const unsigned nb_dfs = (unsigned)((p.n_cta + kDfsWarps - 1) / kDfsWarps);
     roots_top_dfs_kernel<T><<<nb_top, 32 * kTopDfsWarps, smem_top, stream>>>(p, ws);
-    roots_leaves_kernel<T><<<nb_dfs, 32 * kDfsWarps, smem, stream>>>(p, ws);
+    int rc;
+    switch (p.W == 5 ? p.Q : 0) {
+        case 4: rc = launch_leaves_q<T, 4>(p, ws, smem, stream); break;
+        case 5: rc = launch_leaves_q<T, 5>(p, ws, smem, stream); break;
+        case 6: rc = launch_leaves_q<T, 6>(p, ws, smem, stream); break;
+        case 7: rc = launch_leaves_q<T, 7>(p, ws, smem, stream); break;
+        case 8: rc = launch_leaves_q<T, 8>(p, ws, smem, stream); break;
+        case 9: rc = launch_leaves_q<T, 9>(p, ws, smem, stream); break;
+        default: rc = launch_leaves_q<T, 0>(p, ws, smem, stream); break;
+    }
+    if (rc) return rc;
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
@@ -652,7 +747,9 @@ int launch_roots_batched_t(const BatchView& v, int64_t total_cta, int Q, int max
     if (Q + max_w > kDfsRows) return GBN_ERR_Q;
     const size_t smem = sizeof(T) * warp_smem_elems(Q, max_w, max_stride) * kDfsWarps;
     if (smem > 227 * 1024) return GBN_ERR_Q;
-    if (roots_attr<T>(smem)) return GBN_ERR_CUDA;
+    if (cudaFuncSetAttribute(roots_leaves_kernel_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return GBN_ERR_CUDA;
     const unsigned nb_top = (unsigned)((total_cta + kTopWarps - 1) / kTopWarps);
     const unsigned nb_dfs = (unsigned)((total_cta + kDfsWarps - 1) / kDfsWarps);
     roots_top_kernel_b<T><<<nb_top, 32 * kTopWarps, 0, stream>>>(v);
