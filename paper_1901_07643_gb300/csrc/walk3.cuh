@@ -295,32 +295,22 @@ __device__ __forceinline__ long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Bounded wait for the phase with the given parity; false = watchdog expired.
-// The clock is read only every 64 polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, long long limit_ns,
+// Bounded wait for the phase with the given parity (false = the watchdog
+// expired; the clock is read every 64 polls).  Warp-uniform: every lane
+// polls (one instruction for the warp, the same phase seen by all lanes, each
+// lane's own acquire), so the loop has no divergent branch and no broadcast;
+// only the watchdog's status write is made by lane 0.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity, long long limit_ns,
                                           int* status) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = global_ns();
     for (unsigned n = 1;; ++n) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((n & 63u) == 0) {
-            if (global_ns() - t0 > limit_ns) {
-                atomicOr(status, GBN_STATUS_WATCHDOG);
-                return false;
-            }
-            __nanosleep(128);
+        if ((n & 63u) == 0 && global_ns() - t0 > limit_ns) {
+            if ((threadIdx.x & 31) == 0) atomicOr(status, GBN_STATUS_WATCHDOG);
+            return false;
         }
     }
-}
-// Warp-uniform form: lane 0 polls, every lane gets the same answer, and the
-// __syncwarp orders lane 0's acquire before the other lanes' later reads.
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity, long long limit_ns,
-                                          int* status) {
-    int ok = 1;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, limit_ns, status) ? 1 : 0;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    __syncwarp();
-    return ok != 0;
 }
 
 // Timing builds (-DGBN_TIMING) add the cycles each role spends in total and
@@ -750,8 +740,9 @@ __device__ __forceinline__ bool replay_pair(const WalkArgs<float>& a, const floa
         const float2 c2 = make_float2(cs.x, cs.y), s2 = make_float2(cs.z, cs.w);
         const float2 x = zz[i], y = zz[i + 1];
         zz[i] = __ffma2_rn(c2, x, __fmul2_rn(s2, y));
-        const float2 sx = __fmul2_rn(s2, x);
-        const float2 yn = __ffma2_rn(c2, y, make_float2(-sx.x, -sx.y));
+        // -(s x) as one packed multiply by -1 (exact), not two scalar negations
+        const float2 nsx = __fmul2_rn(__fmul2_rn(s2, x), f2(-1.f));
+        const float2 yn = __ffma2_rn(c2, y, nsx);
         zz[i + 1] = yn;
         const float2 wn = __ffma2_rn(yn, yn, ww[i + 2]);
         ww[i + 1] = wn;
