@@ -409,13 +409,14 @@ __device__ __forceinline__ void produce_step(T (&R)[Q * Q], T& c_out, T& s_out) 
 // stays a state machine: a version unrolled over all 2^Q - Q - 1 steps (swaps
 // as register renames, no row table) measured 20-30 % slower at Q = 6, 7 --
 // its code does not stay in the instruction cache beside the consumers'.
-// SLOT < 0: the tape holds (c, s) per step and lane.  SLOT 0 or 1: two
-// producers share a tape of (c0, c1, s0, s1) per step and lane (the paired
-// walk), this one writing component SLOT of each pair.
-template <typename T, int Q, int SLOT = -1>
+// PAIR false: the tape holds (c, s) per step and lane.  PAIR true (the
+// paired walk): the tape holds four words per step and consumer lane,
+// (c_x, c_y, s_x, s_y), and this lane writes its c to word tl and its s to
+// word tl + 2 of each step's 128.
+template <typename T, int Q, bool PAIR = false>
 __device__ __forceinline__ void produce(const WalkArgs<T>& a, const StepTab<Q>& tab,
                                         const T* __restrict__ rec, unsigned char* tape_base,
-                                        uint64_t* full, int lane, bool active) {
+                                        uint64_t* full, int lane, bool active, int tl = 0) {
     using T2 = typename Vec2T<T>::type;
     constexpr int N = StepTab<Q>::N;
     T2* tape = reinterpret_cast<T2*>(tape_base);
@@ -435,11 +436,11 @@ __device__ __forceinline__ void produce(const WalkArgs<T>& a, const StepTab<Q>& 
 #define GBN_PSTEP(r, UP, DOWN)                                                     \
     if (r < Q - 1) {                                                               \
         produce_step<T, Q, (r < Q - 1 ? r : 0)>(R, c, s);                          \
-        if constexpr (SLOT < 0) {                                                  \
+        if constexpr (!PAIR) {                                                     \
             tape[t * 32 + lane] = wk_pair(c, s);                                   \
         } else {                                                                   \
-            tape4[(t * 32 + lane) * 4 + SLOT] = c;                                 \
-            tape4[(t * 32 + lane) * 4 + 2 + SLOT] = s;                             \
+            tape4[t * 128 + tl] = c;                                               \
+            tape4[t * 128 + tl + 2] = s;                                           \
         }                                                                          \
         if (++t == N) goto p_done;                                                 \
         if (t % kChunk == 0) {                                                     \
@@ -683,20 +684,45 @@ __device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
 
 #ifdef GBN_Q
 // ---------------------------------------------------------------- paired walk
-// Two sub-walks per lane: those of two neighbouring roots CTAs (front sets
-// differing in fixed variable W only).  The rotations of both come from one
-// tape entry (c0, c1, s0, s1), a column's entries of both sub-walks sit in
-// one float2, and every rotation, tail sum and score is one packed FP32
-// operation for the two families; the two scores go to slots a constant
-// byte distance apart.  Same block/chain structure as replay_split.
+// A block takes the 64 sub-walks of roots CTAs 2c and 2c+1 (W = 5: fixed
+// variables 0..4 vary over a CTA's lanes, variable 5 tells the two CTAs
+// apart).  Consumer lane l (the "pair lane") carries two sub-walks, x and y,
+// whose front sets differ in fixed variable 0 only:
+//     F_x = (c << 6) | (l << 1),  F_y = F_x | 1,
+// that is roots CTA 2c + (l >> 4), CTA lanes 2 (l & 15) and 2 (l & 15) + 1.
+// A column's entries of both sit in one float2 and every rotation, tail sum
+// and score is one packed FP32 operation for the two families.  Because
+// variable 0 is the lowest, the two scores of every column but variable 0's
+// land in adjacent table slots (one 8-byte store); variable 0 is a child of
+// x only (one 4-byte store).  The tape holds (c_x, c_y, s_x, s_y) per step
+// and pair lane.  Same block/chain structure as replay_split.
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+// Tape word (of a step's 128) of producer warp h's lane: its sub-walk is
+// pair lane (h << 4) | (lane >> 1), component x (even lane) or y (odd lane).
+__device__ __forceinline__ int pair_tape_word(int h, int lane) {
+    return (((h << 4) | (lane >> 1)) << 2) | (lane & 1);
+}
+
+// Store both scores (8 bytes at base + cT * stride) when on_xy, or only x's
+// (4 bytes) when on_x, if cT is a slot; the address is one wide multiply-add
+// and the predicates are formed inside the store's own asm.
+__device__ __forceinline__ void st_pair(char* base, unsigned stride, unsigned cT, float2 v,
+                                        unsigned on_xy, unsigned on_x) {
+    char* addr = base + (size_t)cT * stride;
+    asm volatile(
+        "{\n\t.reg .pred q, r, a, b;\n\tsetp.ne.u32 q, %4, 0;\n\tsetp.ne.u32 r, %5, 0;\n\t"
+        "setp.ne.and.u32 a, %3, 65535, q;\n\tsetp.ne.and.u32 b, %3, 65535, r;\n\t"
+        "@a st.global.v2.f32 [%0], {%1, %2};\n\t@b st.global.f32 [%0], %1;\n\t}"
+        :
+        : "l"(addr), "f"(v.x), "f"(v.y), "r"(cT), "r"(on_xy), "r"(on_x));
+}
 
 template <int Q, int H>
 __device__ __forceinline__ bool replay_pair(const WalkArgs<float>& a, const float4* tape,
                                             uint64_t* full, unsigned par, float2 (&z)[Q], float2 cres,
-                                            int ell,
-                                            int jj, int sh, char* base, unsigned off1, float2 penb,
-                                            unsigned on0, unsigned on1) {
+                                            int ell, int jj, int sh, char* base, float2 penb,
+                                            unsigned on_xy, unsigned on_x) {
     static_assert(Q == GBN_Q, "the step tables in constant memory are this unit's");
     constexpr int N = StepTab<Q>::N;
     constexpr int last_chunk = (N - 1) / kChunk;
@@ -716,14 +742,13 @@ __device__ __forceinline__ bool replay_pair(const WalkArgs<float>& a, const floa
         if (cT != kNotChild) {
             const size_t e0 = (size_t)(base - reinterpret_cast<char*>(a.out)) / 4 +
                               (size_t)cT * (stride / 4);
-            if (on0 && GBN_IN(a.chk, 332, e0, a.out_size))
-                *reinterpret_cast<float*>(base + (size_t)cT * stride) = sc.x;
-            if (on1 && GBN_IN(a.chk, 333, e0 + off1 / 4, a.out_size))
-                *reinterpret_cast<float*>(base + off1 + (size_t)cT * stride) = sc.y;
+            float* p = reinterpret_cast<float*>(base + (size_t)cT * stride);
+            if ((on_xy || on_x) && GBN_IN(a.chk, 332, e0, a.out_size)) p[0] = sc.x;
+            if (on_xy && GBN_IN(a.chk, 333, e0 + 1, a.out_size)) p[1] = sc.y;
+            if (on_xy && (e0 & 1)) GBN_IN(a.chk, 334, e0, 0);  // an 8-byte store must be aligned
         }
 #else
-        st_slot(base, stride, cT, sc.x, on0);
-        st_slot(base + off1, stride, cT, sc.y, on1);
+        st_pair(base, stride, cT, sc, on_xy, on_x);
 #endif
     };
     static_for(std::make_integer_sequence<int, Q + 1>{}, [&](auto sc) {  // the roots' families
@@ -795,11 +820,12 @@ __device__ __forceinline__ bool replay_pair(const WalkArgs<float>& a, const floa
 }
 
 // Consumers of the paired walk.  Items: the Q free variables; the fixed
-// variables above W outside the pair's front sets (both sub-walks); fixed
-// variable W (the first sub-walk only: it is in the second one's front set);
-// the lowest W variables in lane groups (both sub-walks).
-// The warp takes items first, first + stride, ...; returns the number of
-// items of the pair, or -1 when a wait expired.
+// variables above 5 outside the pair's front sets; variables 1..5 in groups
+// of 16 pair lanes (those without the variable in F); variable 0 (x only).
+// Pair lane l reads its column from record 2c + (l >> 4) at CTA lanes
+// 2 (l & 15) and 2 (l & 15) + 1 (one 8-byte load).  The warp takes items
+// first, first + stride, ...; returns the number of items of the pair, or -1
+// when a wait expired.
 template <int Q>
 __device__ __forceinline__ int consume_pair(const WalkArgs<float>& a, const float* __restrict__ rec0,
                                             const float* __restrict__ rec1, const float4* tape,
@@ -807,71 +833,65 @@ __device__ __forceinline__ int consume_pair(const WalkArgs<float>& a, const floa
                                             int stride, uint64_t pc) {
     constexpr int LQ = Q * (Q + 1) / 2;
     constexpr int H = split_levels(Q);
-    const int W = a.W;
-    const uint64_t Fhi0 = (pc << 1) << W;  // the first sub-walk's fixed bits above W
-    const int nu = (a.k - W - 1) - __popcll(pc);  // variables above W, outside both front sets
-    const int g = a.lanes >> 1;
-    const int vpi = 32 / g;
-    const int n5 = (W + vpi - 1) / vpi;
-    const int nitems = Q + nu + 1 + n5;
+    const int nu = (a.k - 6) - __popcll(pc);  // fixed variables above 5 outside F
+    const int nitems = Q + nu + 3 + 1;
     char* out = reinterpret_cast<char*>(a.out);
     const float lnn = a.lnn;
     // penalty bases of the two sub-walks, rounded as the single walk rounds them
-    auto pen2 = [&](uint64_t F0) {
-        const float c0 = float(__popcll(F0));
+    auto pen2 = [&](uint64_t Fx) {
+        const float c0 = float(__popcll(Fx));
         return make_float2(fmaf(c0, lnn, -a.nlnn), fmaf(c0 + 1.f, lnn, -a.nlnn));
     };
-    // entry ix of both records (the second one is never past the first's stride)
-    auto ld2 = [&](size_t ix, bool on, int site) {
-        return (on && GBN_IN(a.chk, site, ix, a.leaf_stride)) ? make_float2(rec0[ix], rec1[ix])
-                                                             : make_float2(0.f, 0.f);
-    };
-    auto load2 = [&](float2 (&z)[Q], float2& cres, size_t e_base, int ell, bool on) {
-#pragma unroll
-        for (int e = 0; e < Q; ++e) z[e] = ld2(e_base + (size_t)e * 32 + ell, on, 331);
-        cres = ld2(e_base + (size_t)Q * 32 + ell, on, 331);
+    // entry ix (of a record's per-lane layout, CTA lane 0) of pair lane pl: x and y
+    auto ld2 = [&](size_t ix, int pl, bool on, int site) {
+        const float* r = (pl >> 4) ? rec1 : rec0;
+        const size_t e = ix + 2 * (size_t)(pl & 15);
+        return (on && GBN_IN(a.chk, site, e + 1, a.leaf_stride))
+                   ? *reinterpret_cast<const float2*>(r + e)
+                   : make_float2(0.f, 0.f);
     };
     for (int it = first; it < nitems; it += stride) {
         // the item's column, then one replay call site (its code is the walk's size)
         float2 z[Q], cres = make_float2(0.f, 0.f);
-        int ell = lane, jj = Q, sh = a.k - 1;
-        unsigned off1, on0 = 1u, on1 = 1u;
-        size_t slot0;  // table element of the first sub-walk's prefix-0 family
+        int pl = lane, jj = Q, sh = a.k - 1;
+        unsigned on_xy = 1u, on_x = 0u;
+        size_t slot;  // table element of x's prefix-0 family
         if (it < Q) {  // free variable j
             const int j = it;
 #pragma unroll
-            for (int e = 0; e < Q; ++e)
-                z[e] = ld2((size_t)(j * (j + 1) / 2 + e) * 32 + lane, e <= j, 330);
+            for (int e = 0; e < Q; ++e) z[e] = ld2((size_t)(j * (j + 1) / 2 + e) * 32, pl, e <= j, 330);
             jj = j;
             sh = a.k;
-            off1 = 4u << W;
-            slot0 = ((size_t)(a.k + j) << (a.m - 1)) + (Fhi0 | (uint64_t)lane);
+            slot = ((size_t)(a.k + j) << (a.m - 1)) + ((pc << 6) | ((uint64_t)pl << 1));
         } else {  // a fixed variable v outside the front sets
             int v;
             bool on = true;
-            if (it < Q + nu + 1) {  // above W, or W itself (the first sub-walk only)
-                const int idx = it - Q;
-                v = idx < nu ? W + 1 + nth_zero_bit(pc, idx) : W;
-                off1 = v > W ? (4u << W) : 0u;
-                on1 = v > W ? 1u : 0u;
-            } else {  // the lowest W variables, a group of lanes each
-                const int j = it - Q - nu - 1;
-                const int uu = lane / g, sub = lane % g;
-                v = j * vpi + uu;
-                on = v < W;
-                ell = on ? ((sub & ((1 << v) - 1)) | ((sub >> v) << (v + 1))) : 0;
-                if (!on) v = 0;
-                off1 = 4u << (W - 1);
-                on0 = on1 = on ? 1u : 0u;
+            if (it < Q + nu) {  // above 5
+                v = 6 + nth_zero_bit(pc, it - Q);
+            } else if (it < Q + nu + 3) {  // 1..5, 16 pair lanes each (bit v-1 of pl clear)
+                const int j = it - Q - nu;
+                const int uu = lane >> 4, sub = lane & 15;
+                v = 1 + 2 * j + uu;
+                on = v <= 5;
+                const int b = on ? v - 1 : 0;
+                pl = (sub & ((1 << b) - 1)) | ((sub >> b) << (b + 1));
+                if (!on) v = 1;
+                on_xy = on ? 1u : 0u;
+            } else {  // variable 0: a child of x only
+                v = 0;
+                on_xy = 0u;
+                on_x = 1u;
             }
-            load2(z, cres, (size_t)32 * (LQ + v * (Q + 1)), ell, on);
-            const uint64_t F0 = Fhi0 | (uint64_t)ell;
+            const size_t b0 = (size_t)32 * (LQ + v * (Q + 1));
+#pragma unroll
+            for (int e = 0; e < Q; ++e) z[e] = ld2(b0 + (size_t)e * 32, pl, on, 331);
+            cres = ld2(b0 + (size_t)Q * 32, pl, on, 331);
+            const uint64_t Fx = (pc << 6) | ((uint64_t)pl << 1);
             const uint64_t lowmask = (1ull << v) - 1ull;
-            slot0 = ((size_t)v << (a.m - 1)) + ((F0 & lowmask) | ((F0 >> (v + 1)) << v));
+            slot = ((size_t)v << (a.m - 1)) + ((Fx & lowmask) | ((Fx >> (v + 1)) << v));
         }
-        const bool ok = replay_pair<Q, H>(a, tape, full, par, z, cres, ell, jj, sh,
-                                          out + slot0 * 4, off1, pen2(Fhi0 | (uint64_t)ell), on0,
-                                          on1);
+        const bool ok = replay_pair<Q, H>(a, tape, full, par, z, cres, pl, jj, sh, out + slot * 4,
+                                          pen2((pc << 6) | ((uint64_t)pl << 1)), on_xy, on_x);
         if (!ok) return -1;
     }
     return nitems;
@@ -1028,10 +1048,9 @@ __global__ void __launch_bounds__(kPairThreads, Q >= 8 ? 1 : 3) walk_kernel_pair
     const uint64_t pc = blockIdx.x;
     const float* rec0 = a.leaves + (size_t)(2 * pc) * a.leaf_stride;
     const float* rec1 = rec0 + a.leaf_stride;
-    if (warp == 0)
-        produce<float, Q, 0>(a, c_steps, rec0, smem + S::off_tape, full, lane, true);
-    else if (warp == 1)
-        produce<float, Q, 1>(a, c_steps, rec1, smem + S::off_tape, full, lane, true);
+    if (warp < 2)
+        produce<float, Q, true>(a, c_steps, warp ? rec1 : rec0, smem + S::off_tape, full, lane,
+                                true, pair_tape_word(warp, lane));
     else
         consume_pair<Q>(a, rec0, rec1, reinterpret_cast<const float4*>(smem + S::off_tape), full,
                         0u, lane, warp - 2, a.n_cwarps, pc);
@@ -1101,10 +1120,8 @@ __global__ void __launch_bounds__(ring_threads<Q, PAIR>(),
             uint64_t* fb = full + s * S::chunks;
             if constexpr (PAIR) {
                 const float* rec = a.leaves + (size_t)(2 * u + warp) * a.leaf_stride;
-                if (warp == 0)
-                    produce<float, Q, 0>(a, c_steps, rec, tb, fb, lane, true);
-                else
-                    produce<float, Q, 1>(a, c_steps, rec, tb, fb, lane, true);
+                produce<float, Q, true>(a, c_steps, rec, tb, fb, lane, true,
+                                        pair_tape_word(warp, lane));
             } else {
                 const float* rec = a.leaves + (size_t)u * a.leaf_stride;
                 produce<float, Q>(a, c_steps, rec, tb, fb, lane, lane < a.lanes);
