@@ -595,20 +595,31 @@ __host__ __device__ __forceinline__ size_t leaf_warp_elems(const Plan& p) {
                                               : warp_smem_elems(p.Q, p.W, p.leaf_stride);
 }
 
+// The FP32 form (REG) gives a walk CTA two warps: half 0 / 1 takes the
+// exclude / include branch of the first leaf level and the 16 leaves below
+// it, so that twice as many warps share the chains of rotations.  The FP64
+// form (shared-memory stack) enumerates all 32 leaves in one warp.
 template <typename T, int Q, bool REG>
 __device__ __forceinline__ void leaves_w5(const T* __restrict__ top, const Plan& p,
                                           T* __restrict__ leaves, unsigned long long* chk,
-                                          uint64_t cta, T* stack) {
+                                          uint64_t cta, T* stack, int half = -1) {
     constexpr int RT = Q + 5;
     const int lane = threadIdx.x & 31;
     T M[RT];
     T C;
     unsigned carried;
     load_n<T, RT, RT>(top + (size_t)cta * node_elems(RT), M, C, carried, lane);
-    if constexpr (REG)  // staging at the start of the warp's shared memory
-        Dfs5R<T, Q, 0>::run(M, C, carried, lane, p.k - 5, 0, stack, p,
-                            leaves + (size_t)cta * p.leaf_stride, chk);
-    else
+    if constexpr (REG) {  // staging at the start of the warp's shared memory
+        T* rec = leaves + (size_t)cta * p.leaf_stride;
+        const int topk = p.k - 5;
+        if (half) {
+            include_n<T, RT, RT>(M);
+        } else {
+            carried |= 1u << topk;
+            exclude_r<T, RT, RT>(M, C, topk, (carried >> lane) & 1u);
+        }
+        Dfs5R<T, Q, 1>::run(M, C, carried, lane, topk, half << 4, stack, p, rec, chk);
+    } else
         Dfs5<T, Q, 0>::run(M, C, carried, lane, p.k - 5, 0, stack, p,
                            leaves + (size_t)cta * p.leaf_stride, chk);
 }
@@ -655,17 +666,21 @@ __global__ void __launch_bounds__(32 * kTopDfsWarps) roots_top_dfs_kernel(const 
 // with the stack in registers, FP64 in shared memory), or 0 for the generic
 // one; each instance gets the registers its own Q needs.
 template <typename T, int QF>
-__global__ void __launch_bounds__(32 * kDfsWarps) roots_leaves_kernel(const Plan p, char* ws) {
+__global__ void __launch_bounds__(32 * kDfsWarps, (std::is_same<T, float>::value && QF > 0) ? 6 : 1)
+    roots_leaves_kernel(const Plan p, char* ws) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
-    const uint64_t cta = (uint64_t)blockIdx.x * kDfsWarps + warp;
+    constexpr bool kReg = std::is_same<T, float>::value && QF > 0;
+    constexpr int kWarpsPerCta = kReg ? 2 : 1;
+    const uint64_t gw = (uint64_t)blockIdx.x * kDfsWarps + warp;
+    const uint64_t cta = gw / kWarpsPerCta;
     if (cta >= (uint64_t)p.n_cta) return;
     T* stack = reinterpret_cast<T*>(smem_raw) + warp * leaf_warp_elems<T>(p);
     T* leaves = reinterpret_cast<T*>(ws + p.off_leaves);
     unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
     if constexpr (QF > 0)
-        leaves_w5<T, QF, std::is_same<T, float>::value>(top_nodes<T>(p, ws), p, leaves, chk, cta,
-                                                         stack);
+        leaves_w5<T, QF, kReg>(top_nodes<T>(p, ws), p, leaves, chk, cta, stack,
+                               kReg ? (int)(gw & 1) : -1);
     else
         leaves_body<T>(top_nodes<T>(p, ws), p, leaves, chk, cta, stack);
 }
@@ -710,7 +725,8 @@ int launch_leaves_q(const Plan& p, char* ws, size_t smem, cudaStream_t stream) {
     if (cudaFuncSetAttribute(roots_leaves_kernel<T, QF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return GBN_ERR_CUDA;
-    const unsigned nb = (unsigned)((p.n_cta + kDfsWarps - 1) / kDfsWarps);
+    const int warps_per_cta = (std::is_same<T, float>::value && QF > 0) ? 2 : 1;
+    const unsigned nb = (unsigned)((p.n_cta * warps_per_cta + kDfsWarps - 1) / kDfsWarps);
     roots_leaves_kernel<T, QF><<<nb, 32 * kDfsWarps, smem, stream>>>(p, ws);
     return GBN_OK;
 }

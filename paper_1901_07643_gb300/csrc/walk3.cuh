@@ -1034,7 +1034,8 @@ __global__ void __launch_bounds__(32 * (1 + kMaxConsumerWarps)) walk_kernel_b(co
 // The paired FP32 walk: block c runs the sub-walks of roots CTAs 2c and 2c+1
 // (W = 5).  Warps 0 and 1 produce the two halves of the tape, the others
 // consume both sub-walks at once.
-constexpr int kPairThreads = 32 * (2 + kMaxConsumerWarps);
+constexpr int kPairConsumerWarps = 8;
+constexpr int kPairThreads = 32 * (2 + kPairConsumerWarps);
 constexpr size_t kPairMaxSmem = 160 * 1024;  // the tape of Q = 9 does not fit
 template <int Q>
 __global__ void __launch_bounds__(kPairThreads, Q >= 8 ? 1 : 3) walk_kernel_pair(const WalkArgs<float> a) {
@@ -1053,7 +1054,7 @@ __global__ void __launch_bounds__(kPairThreads, Q >= 8 ? 1 : 3) walk_kernel_pair
                                 true, pair_tape_word(warp, lane));
     else
         consume_pair<Q>(a, rec0, rec1, reinterpret_cast<const float4*>(smem + S::off_tape), full,
-                        0u, lane, warp - 2, a.n_cwarps, pc);
+                        0u, lane, warp - 2, (int)(blockDim.x >> 5) - 2, pc);
 }
 
 // Whether a launch takes the paired walk: FP32 scores, full warps of
@@ -1205,7 +1206,8 @@ int launch_walk_q(const WalkArgs<T>& a, int64_t n_cta, cudaStream_t stream) {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem_p) != cudaSuccess)
                 return GBN_ERR_CUDA;
-            walk_kernel_pair<Q><<<(unsigned)(n_cta / 2), 32 * (2 + a.n_cwarps), smem_p, stream>>>(a);
+            const int ncw = a.n_cwarps < kPairConsumerWarps ? a.n_cwarps : kPairConsumerWarps;
+            walk_kernel_pair<Q><<<(unsigned)(n_cta / 2), 32 * (2 + ncw), smem_p, stream>>>(a);
             return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
         }
     }
