@@ -338,8 +338,18 @@ __host__ __device__ __forceinline__ size_t dfs_stack_elems(int Q, int W) {
 
 // One warp's shared memory in the leaf kernel: the stack, then 8 staged
 // leaf records.
+// The staging of eight leaf records: element e of leaf j (0..7) at
+// e * 8 + j + (e >> 3).  Without the skew the lanes of one store (one column
+// each, entries e a multiple of 8 apart for the fixed variables when Q + 1 is
+// 8) all hit one shared-memory bank.
+__host__ __device__ __forceinline__ int stage_index(int e, int j) { return e * 8 + j + (e >> 3); }
+__host__ __device__ __forceinline__ size_t stage_elems(size_t leaf_stride) {
+    const size_t R = leaf_stride / 32;
+    return R * 8 + R / 8 + 1;
+}
+
 __host__ __device__ __forceinline__ size_t warp_smem_elems(int Q, int W, size_t leaf_stride) {
-    return dfs_stack_elems(Q, W) + (leaf_stride / 32) * 8;
+    return dfs_stack_elems(Q, W) + stage_elems(leaf_stride);
 }
 
 template <typename T>
@@ -457,7 +467,7 @@ __device__ __forceinline__ void write_leaf_q(const T (&M)[RT], T C, const Plan& 
     }
 }
 
-// Stage leaf ell's record in shared memory, stg[e * 8 + (ell & 7)]; after
+// Stage leaf ell's record in shared memory, stg[stage_index(e, ell & 7)]; after
 // the eighth leaf of a group (the enumeration runs ell = 31 down to 0) write
 // the group out as 8-float runs, one full 32-byte sector per record element.
 template <typename T, int Q, int RT>
@@ -471,22 +481,22 @@ __device__ __forceinline__ void stage_leaf_q(const T (&M)[RT], T C, const Plan& 
         const int e0 = i * (i + 1) / 2;
         sfor(std::make_integer_sequence<int, Q>{}, [&](auto rc) {
             constexpr int r = decltype(rc)::value;
-            if (r <= i) stg[(e0 + r) * 8 + j] = M[r];
+            if (r <= i) stg[stage_index(e0 + r, j)] = M[r];
         });
     } else if (lane < k && ((carried_mask >> lane) & 1u)) {  // fixed variable in B
         const int e0 = LQ + var_of_lane(p, lane) * (Q + 1);
         sfor(std::make_integer_sequence<int, Q>{}, [&](auto rc) {
             constexpr int r = decltype(rc)::value;
-            stg[(e0 + r) * 8 + j] = M[r];
+            stg[stage_index(e0 + r, j)] = M[r];
         });
-        stg[(e0 + Q) * 8 + j] = C;
+        stg[stage_index(e0 + Q, j)] = C;
     }
     if (j == 0) {  // the group ell .. ell + 7 is complete
         __syncwarp();
         const int R = (int)(p.leaf_stride / 32);
         for (int idx = lane; idx < R * 8; idx += 32) {
             const size_t ix = (size_t)(idx >> 3) * 32 + ell + (idx & 7);
-            if (GBN_IN(chk, 227, ix, p.leaf_stride)) rec[ix] = stg[idx];
+            if (GBN_IN(chk, 227, ix, p.leaf_stride)) rec[ix] = stg[stage_index(idx >> 3, idx & 7)];
         }
         __syncwarp();
     }
@@ -591,7 +601,7 @@ __host__ __device__ __forceinline__ bool leaves_in_registers(int Q, int W) {
 }
 template <typename T>
 __host__ __device__ __forceinline__ size_t leaf_warp_elems(const Plan& p) {
-    return leaves_in_registers<T>(p.Q, p.W) ? (p.leaf_stride / 32) * 8
+    return leaves_in_registers<T>(p.Q, p.W) ? stage_elems(p.leaf_stride)
                                               : warp_smem_elems(p.Q, p.W, p.leaf_stride);
 }
 
