@@ -21,16 +21,20 @@ namespace {
 constexpr int kFixWarps = 4;
 constexpr int kLdF = 33;
 
-__global__ void fix_flags_kernel(const Plan p, char* ws) {
+// 32 warps load R0 (one element per thread, one round of loads); warp 0 does
+// the rest.
+__global__ void __launch_bounds__(1024) fix_flags_kernel(const Plan p, char* ws) {
     __shared__ float R[32 * kLdF];
     __shared__ float Ri[32 * kLdF];
-    const int lane = threadIdx.x, m = p.m;
+    const int lane = threadIdx.x & 31, m = p.m;
     const double* R0 = reinterpret_cast<const double*>(ws + p.off_r0);
-    for (int r = 0; r < 32; ++r) {
+    {
+        const int r = threadIdx.x >> 5;
         R[r * kLdF + lane] = (r < m && lane < m) ? (float)R0[r * m + lane] : 0.f;
         Ri[r * kLdF + lane] = 0.f;
     }
-    __syncwarp();
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
     if (lane < m) {  // column `lane` of R0^{-1}
         for (int i = lane; i >= 0; --i) {
             float s = (i == lane) ? 1.f : 0.f;
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(32 * kFixWarps) fixup_kernel(const Plan p, cha
 }  // namespace
 
 int launch_fix_flags(const Plan& p, char* ws, cudaStream_t stream) {
-    fix_flags_kernel<<<1, 32, 0, stream>>>(p, ws);
+    fix_flags_kernel<<<1, 1024, 0, stream>>>(p, ws);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 

@@ -15,7 +15,8 @@ namespace {
 
 constexpr int kPanelChunk = 64;  // rows staged in shared memory at a time
 constexpr int kLd = 33;          // row stride of the m x m shared-memory tiles
-constexpr int kRedThreads = 1024; // threads of the reduction / Cholesky kernel
+constexpr int kRedThreads = 1024; // threads of the reduction kernels
+constexpr int kCholThreads = 1024;  // threads of the Cholesky kernel (one barrier per column)
 
 // All shared-memory tiles here are flat 1-D arrays indexed as [row * kLd + col]:
 // with this toolchain, runtime-indexed two-dimensional __shared__ arrays were
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(kRedThreads) gram_sum_kernel(const Plan p, cha
     const R0Ptrs q = r0_ptrs(p, ws);
     gram_sum_body(blockIdx.x, q.gram, p.panels, p.m, q.gsum, q.chk);
 }
-__global__ void __launch_bounds__(kRedThreads) chol_kernel(const Plan p, char* ws, int pass) {
+__global__ void __launch_bounds__(kCholThreads) chol_kernel(const Plan p, char* ws, int pass) {
     const R0Ptrs q = r0_ptrs(p, ws);
     if (pass)
         chol_body(q.gsum, p.m, q.r1, q.r0, nullptr, q.status, q.chk);
@@ -368,7 +369,7 @@ __global__ void __launch_bounds__(kRedThreads) gram_sum_kernel_b(const BatchView
     const R0Ptrs q = r0_ptrs(p, v.ws[d]);
     gram_sum_body(blockIdx.x, q.gram, p.panels, p.m, q.gsum, q.chk);
 }
-__global__ void __launch_bounds__(kRedThreads) chol_kernel_b(const BatchView v, int pass) {
+__global__ void __launch_bounds__(kCholThreads) chol_kernel_b(const BatchView v, int pass) {
     const int d = blockIdx.x;
     const Plan& p = v.plans[d];
     const R0Ptrs q = r0_ptrs(p, v.ws[d]);
@@ -387,10 +388,10 @@ int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream) {
     const unsigned groups = (unsigned)((p.m * (p.m + 1) / 2 + 31) / 32);
     gram_kernel<<<p.panels, 512, 0, stream>>>(p, X, ws, 0);
     gram_sum_kernel<<<groups, kRedThreads, 0, stream>>>(p, ws);
-    chol_kernel<<<1, kRedThreads, 0, stream>>>(p, ws, 0);
+    chol_kernel<<<1, kCholThreads, 0, stream>>>(p, ws, 0);
     gram_kernel<<<p.panels, 512, 0, stream>>>(p, X, ws, 1);
     gram_sum_kernel<<<groups, kRedThreads, 0, stream>>>(p, ws);
-    chol_kernel<<<1, kRedThreads, 0, stream>>>(p, ws, 1);
+    chol_kernel<<<1, kCholThreads, 0, stream>>>(p, ws, 1);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
@@ -402,10 +403,10 @@ int launch_r0_batched(const BatchView& v, int64_t total_panels, int max_m, cudaS
     const dim3 sum_grid((unsigned)((max_m * (max_m + 1) / 2 + 31) / 32), B);
     gram_kernel_b<<<P, 512, 0, stream>>>(v, 0);
     gram_sum_kernel_b<<<sum_grid, kRedThreads, 0, stream>>>(v);
-    chol_kernel_b<<<B, kRedThreads, 0, stream>>>(v, 0);
+    chol_kernel_b<<<B, kCholThreads, 0, stream>>>(v, 0);
     gram_kernel_b<<<P, 512, 0, stream>>>(v, 1);
     gram_sum_kernel_b<<<sum_grid, kRedThreads, 0, stream>>>(v);
-    chol_kernel_b<<<B, kRedThreads, 0, stream>>>(v, 1);
+    chol_kernel_b<<<B, kCholThreads, 0, stream>>>(v, 1);
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
