@@ -221,6 +221,11 @@ extern "C" int score_all_families_batched(const double* const* Xs, const int64_t
     v.ws = reinterpret_cast<char* const*>(base + L.off_ws);
     v.out = reinterpret_cast<void* const*>(base + L.off_out);
     v.walk_args = base + L.off_args;
+    v.pairs = (precision == 0 && opts->debug_coverage == 0) ? 1 : 0;
+    for (int b = 0; b < B && v.pairs; ++b) {  // the paired walk's conditions, for every dataset
+        const Plan& pb = L.plans[b];
+        if (pb.W != 5 || pb.lanes != 32 || pb.n_cta % 2 != 0) v.pairs = 0;
+    }
     int max_m = 1;
     for (int b = 0; b < B; ++b) max_m = std::max(max_m, L.plans[b].m);
     if ((rc = launch_r0_batched(v, L.total_panels, max_m, stream))) return rc;

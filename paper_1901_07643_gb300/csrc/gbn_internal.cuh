@@ -123,6 +123,7 @@ struct BatchView {
     char* const* ws = nullptr;              // per-dataset workspace region
     void* const* out = nullptr;             // per-dataset score table
     const void* walk_args = nullptr;        // WalkArgs<T>[B]
+    int pairs = 0;                          // every dataset takes the paired FP32 walk
 };
 
 // Dataset index for global block bx: the launch position l with

@@ -1038,7 +1038,7 @@ constexpr int kPairConsumerWarps = 8;
 constexpr int kPairThreads = 32 * (2 + kPairConsumerWarps);
 constexpr size_t kPairMaxSmem = 160 * 1024;  // the tape of Q = 9 does not fit
 template <int Q>
-__global__ void __launch_bounds__(kPairThreads, Q >= 8 ? 1 : 3) walk_kernel_pair(const WalkArgs<float> a) {
+__device__ __forceinline__ void walk_pair_body(const WalkArgs<float>& a, uint64_t pc) {
     extern __shared__ __align__(16) unsigned char smem[];
     using S = SmemP<Q>;
     static_assert(Q == GBN_Q, "one Q per translation unit");
@@ -1046,7 +1046,6 @@ __global__ void __launch_bounds__(kPairThreads, Q >= 8 ? 1 : 3) walk_kernel_pair
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::off_bar);
     for (int c = threadIdx.x; c < S::chunks; c += blockDim.x) mbar_init(&full[c], 2);
     __syncthreads();
-    const uint64_t pc = blockIdx.x;
     const float* rec0 = a.leaves + (size_t)(2 * pc) * a.leaf_stride;
     const float* rec1 = rec0 + a.leaf_stride;
     if (warp < 2)
@@ -1055,6 +1054,22 @@ __global__ void __launch_bounds__(kPairThreads, Q >= 8 ? 1 : 3) walk_kernel_pair
     else
         consume_pair<Q>(a, rec0, rec1, reinterpret_cast<const float4*>(smem + S::off_tape), full,
                         0u, lane, warp - 2, (int)(blockDim.x >> 5) - 2, pc);
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kPairThreads, Q >= 8 ? 1 : 3) walk_kernel_pair(const WalkArgs<float> a) {
+    walk_pair_body<Q>(a, blockIdx.x);
+}
+
+// A batch in which every dataset takes the paired walk (every CTA count is
+// even, so pair g of the batch is walk CTA 2g): the block finds its dataset
+// through the prefix of walk CTAs and copies that dataset's arguments.
+template <int Q>
+__global__ void __launch_bounds__(kPairThreads, Q >= 8 ? 1 : 3) walk_kernel_pair_b(const BatchView v) {
+    int64_t local;
+    const int d = batch_locate(v, v.cta_prefix, 2 * (int64_t)blockIdx.x, local);
+    const WalkArgs<float> a = static_cast<const WalkArgs<float>*>(v.walk_args)[d];
+    walk_pair_body<Q>(a, (uint64_t)local >> 1);
 }
 
 // Whether a launch takes the paired walk: FP32 scores, full warps of
@@ -1222,6 +1237,18 @@ template <typename T, int Q, bool COV>
 int launch_walk_batched_q(const BatchView& v, int64_t total_cta, int n_cwarps, cudaStream_t stream) {
     const size_t smem = Smem<T, Q>::bytes;
     if (n_cwarps < 1 || n_cwarps > kMaxConsumerWarps) return GBN_ERR_Q;
+    if constexpr (pair_walk_compiled<T, Q, COV>()) {
+        if (v.pairs && total_cta % 2 == 0) {
+            const size_t smem_p = SmemP<Q>::bytes;
+            if (cudaFuncSetAttribute(walk_kernel_pair_b<Q>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_p) != cudaSuccess)
+                return GBN_ERR_CUDA;
+            const int ncw = n_cwarps < kPairConsumerWarps ? n_cwarps : kPairConsumerWarps;
+            walk_kernel_pair_b<Q><<<(unsigned)(total_cta / 2), 32 * (2 + ncw), smem_p, stream>>>(v);
+            return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+        }
+    }
     if (cudaFuncSetAttribute(walk_kernel_b<T, Q, COV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return GBN_ERR_CUDA;

@@ -42,6 +42,25 @@ def test_batched_equals_single_calls(precision):
         assert torch.equal(out[off:off + (m << (m - 1))], single)
 
 
+def test_batched_paired_walk_equals_single_calls():
+    # every dataset has W = 5 and an even number of walk CTAs (m >= q + 6), so
+    # the batch takes the paired walk; single calls at q = 6 take the paired ring
+    Xs = _uneven(5, 17, m_lo=12, m_hi=14, n_lo=40, n_hi=300)
+    Xd = _dev(Xs)
+    out, offs = binding.score_all_families_batched(Xd, q=6)
+    torch.cuda.synchronize()
+    for X, off in zip(Xd, offs):
+        m = X.shape[1]
+        single = binding.score_all_families(X, q=6)
+        assert torch.equal(out[off:off + (m << (m - 1))], single)
+    got = out.double().cpu().numpy()
+    X = Xs[0]
+    n, m = X.shape
+    _, ref = oracle.scores(X)
+    g = got[offs[0]:offs[0] + (m << (m - 1))]
+    assert float((np.abs(g - ref) / np.maximum(np.abs(ref), n)).max()) <= 1e-4
+
+
 def test_batched_against_oracle():
     Xs = _uneven(6, 11, m_hi=10)
     out, offs = binding.score_all_families_batched(_dev(Xs))
