@@ -767,6 +767,39 @@ int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
+// A batch whose datasets all have W = 5 (FP32, a compiled Q): the two-warp
+// register-stack leaf enumeration of the single-dataset kernel, warps finding
+// their dataset through the prefix of walk CTAs.
+template <typename T, int QF>
+__global__ void __launch_bounds__(32 * kDfsWarps, 6)
+    roots_leaves_kernel_bq(const BatchView v, size_t max_stride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * kDfsWarps + warp;
+    const int64_t g = gw >> 1;
+    if (g >= v.cta_prefix[v.B]) return;
+    int64_t local;
+    const int d = batch_locate(v, v.cta_prefix, g, local);
+    const Plan& p = v.plans[d];
+    char* ws = v.ws[d];
+    T* stg = reinterpret_cast<T*>(smem_raw) + warp * stage_elems(max_stride);
+    unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
+    leaves_w5<T, QF, true>(top_nodes<T>(p, ws), p, reinterpret_cast<T*>(ws + p.off_leaves), chk,
+                           (uint64_t)local, stg, (int)(gw & 1));
+}
+
+template <typename T, int QF>
+int launch_leaves_bq(const BatchView& v, int64_t total_cta, size_t max_stride,
+                     cudaStream_t stream) {
+    const size_t smem = sizeof(T) * stage_elems(max_stride) * kDfsWarps;
+    if (cudaFuncSetAttribute(roots_leaves_kernel_bq<T, QF>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return GBN_ERR_CUDA;
+    const unsigned nb = (unsigned)((2 * total_cta + kDfsWarps - 1) / kDfsWarps);
+    roots_leaves_kernel_bq<T, QF><<<nb, 32 * kDfsWarps, smem, stream>>>(v, max_stride);
+    return GBN_OK;
+}
+
 template <typename T>
 int launch_roots_batched_t(const BatchView& v, int64_t total_cta, int Q, int max_w,
                            size_t max_stride, cudaStream_t stream) {
@@ -779,7 +812,24 @@ int launch_roots_batched_t(const BatchView& v, int64_t total_cta, int Q, int max
     const unsigned nb_top = (unsigned)((total_cta + kTopWarps - 1) / kTopWarps);
     const unsigned nb_dfs = (unsigned)((total_cta + kDfsWarps - 1) / kDfsWarps);
     roots_top_kernel_b<T><<<nb_top, 32 * kTopWarps, 0, stream>>>(v);
-    roots_leaves_kernel_b<T><<<nb_dfs, 32 * kDfsWarps, smem, stream>>>(v, Q, max_w, max_stride);
+    bool reg = false;
+    if constexpr (std::is_same<T, float>::value) reg = v.pairs && leaves_in_registers<T>(Q, 5);
+    if (reg) {
+        int rc = GBN_OK;
+        if constexpr (std::is_same<T, float>::value) {
+            switch (Q) {
+                case 4: rc = launch_leaves_bq<T, 4>(v, total_cta, max_stride, stream); break;
+                case 5: rc = launch_leaves_bq<T, 5>(v, total_cta, max_stride, stream); break;
+                case 6: rc = launch_leaves_bq<T, 6>(v, total_cta, max_stride, stream); break;
+                case 7: rc = launch_leaves_bq<T, 7>(v, total_cta, max_stride, stream); break;
+                case 8: rc = launch_leaves_bq<T, 8>(v, total_cta, max_stride, stream); break;
+                default: rc = launch_leaves_bq<T, 9>(v, total_cta, max_stride, stream); break;
+            }
+        }
+        if (rc) return rc;
+    } else {
+        roots_leaves_kernel_b<T><<<nb_dfs, 32 * kDfsWarps, smem, stream>>>(v, Q, max_w, max_stride);
+    }
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
