@@ -82,8 +82,12 @@ __device__ __forceinline__ void gram_body(int blk, const double* __restrict__ X,
     __shared__ double rows[kPanelChunk * kLd];
     __shared__ double qrows[kPanelChunk * kLd];
     __shared__ double ri[32 * kLd];
+    __shared__ int ord[32];  // the plan's column order (the plan may live in global memory)
     const int tid = threadIdx.x;
-    if (tid < m) mu[tid] = mu_g[tid];
+    if (tid < m) {
+        mu[tid] = mu_g[tid];
+        ord[tid] = plan.order[tid];
+    }
     if (Rinv)
         for (int e = tid; e < m * m; e += blockDim.x)
             if (GBN_IN(chk, 112, (e / m) * kLd + e % m, 32 * kLd)) ri[(e / m) * kLd + e % m] = Rinv[e];
@@ -107,7 +111,7 @@ __device__ __forceinline__ void gram_body(int blk, const double* __restrict__ X,
         const int cnt = (rend - c0 < kPanelChunk) ? (int)(rend - c0) : kPanelChunk;
         for (int e = tid; e < cnt * m; e += blockDim.x) {
             const int t = e / m, j = e % m;
-            const int64_t xi = (c0 + t) * m + plan.order[j];
+            const int64_t xi = (c0 + t) * m + ord[j];
             if (GBN_IN(chk, 113, xi, n * m) && GBN_IN(chk, 114, t * kLd + j, kPanelChunk * kLd))
                 rows[t * kLd + j] = X[xi] - mu[j];
         }
