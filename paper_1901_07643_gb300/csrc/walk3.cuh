@@ -249,7 +249,7 @@ __device__ __forceinline__ void st_slot(char* base, unsigned stride, unsigned cT
     char* addr = base + (size_t)cT * stride;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %3, 0;\n\t"
-        "setp.ne.and.u32 p, %2, 65535, q;\n\t@p st.global.f32 [%0], %1;\n\t}"
+        "setp.ne.and.u32 p, %2, 65535, q;\n\t@p st.global.cs.f32 [%0], %1;\n\t}"
         :
         : "l"(addr), "f"(v), "r"(cT), "r"(on));
 }
@@ -258,7 +258,7 @@ __device__ __forceinline__ void st_slot(char* base, unsigned stride, unsigned cT
     char* addr = base + (size_t)cT * stride;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %3, 0;\n\t"
-        "setp.ne.and.u32 p, %2, 65535, q;\n\t@p st.global.f64 [%0], %1;\n\t}"
+        "setp.ne.and.u32 p, %2, 65535, q;\n\t@p st.global.cs.f64 [%0], %1;\n\t}"
         :
         : "l"(addr), "d"(v), "r"(cT), "r"(on));
 }
@@ -706,14 +706,16 @@ __device__ __forceinline__ int pair_tape_word(int h, int lane) {
 
 // Store both scores (8 bytes at base + cT * stride) when on_xy, or only x's
 // (4 bytes) when on_x, if cT is a slot; the address is one wide multiply-add
-// and the predicates are formed inside the store's own asm.
+// and the predicates are formed inside the store's own asm.  The table is
+// written once and not read back here: streaming stores (.cs) measured 2 %
+// faster than default ones.
 __device__ __forceinline__ void st_pair(char* base, unsigned stride, unsigned cT, float2 v,
                                         unsigned on_xy, unsigned on_x) {
     char* addr = base + (size_t)cT * stride;
     asm volatile(
         "{\n\t.reg .pred q, r, a, b;\n\tsetp.ne.u32 q, %4, 0;\n\tsetp.ne.u32 r, %5, 0;\n\t"
         "setp.ne.and.u32 a, %3, 65535, q;\n\tsetp.ne.and.u32 b, %3, 65535, r;\n\t"
-        "@a st.global.v2.f32 [%0], {%1, %2};\n\t@b st.global.f32 [%0], %1;\n\t}"
+        "@a st.global.cs.v2.f32 [%0], {%1, %2};\n\t@b st.global.cs.f32 [%0], %1;\n\t}"
         :
         : "l"(addr), "f"(v.x), "f"(v.y), "r"(cT), "r"(on_xy), "r"(on_x));
 }
