@@ -215,3 +215,20 @@ def test_table_written_straight_to_pinned_host_memory():
     binding.score_all_families(Xt, host)
     torch.cuda.synchronize()
     assert torch.equal(host, dev.cpu())
+
+
+@pytest.mark.parametrize("m,q", [(12, 6), (13, 7), (14, 6), (17, 7), (18, 8), (16, 5)])
+def test_fp32_walk_forms_write_every_slot(m, q):
+    """The FP32 forms for full warps (the paired walk, its persistent ring at
+    q <= 6) over a table first filled with NaN: every slot is written, and the
+    table matches the oracle.  Cases span one pair of roots CTAs (m = q + 6),
+    several persistent units, and q = 5 .. 8."""
+    n = 90
+    X = synthetic.sem_sample(m, n, 0.3, 7000 + 10 * m + q)
+    Xt = torch.from_numpy(X).cuda()
+    out = torch.full((m << (m - 1),), float("nan"), dtype=torch.float32, device="cuda")
+    binding.score_all_families(Xt, out, q=q)
+    torch.cuda.synchronize()
+    assert not bool(torch.isnan(out).any()), "a slot was not written"
+    _, ref = oracle.scores(X)
+    _check(out.cpu().numpy(), ref, n, TOL[0])
