@@ -339,13 +339,18 @@ __host__ __device__ __forceinline__ size_t dfs_stack_elems(int Q, int W) {
 // One warp's shared memory in the leaf kernel: the stack, then 8 staged
 // leaf records.
 // The staging of eight leaf records: element e of leaf j (0..7) at
-// e * 8 + j + (e >> 3).  Without the skew the lanes of one store (one column
-// each, entries e a multiple of 8 apart for the fixed variables when Q + 1 is
-// 8) all hit one shared-memory bank.
-__host__ __device__ __forceinline__ int stage_index(int e, int j) { return e * 8 + j + (e >> 3); }
+// 8 e + j + skew(e), the skew 0 in the L block (e < Q(Q+1)/2) and 1 + v in
+// the block of fixed variable v.  Without it the lanes of one store (one
+// column each, the fixed variables' entries a multiple of Q + 1 apart) hit
+// few banks (one when Q + 1 = 8); with it a lane's entries are 8 apart from
+// a per-lane base, so its stores take immediate offsets.
+template <int Q>
+__device__ __forceinline__ int stage_skew(int e) {
+    constexpr int LQ = Q * (Q + 1) / 2;
+    return e < LQ ? 0 : 1 + (e - LQ) / (Q + 1);
+}
 __host__ __device__ __forceinline__ size_t stage_elems(size_t leaf_stride) {
-    const size_t R = leaf_stride / 32;
-    return R * 8 + R / 8 + 1;
+    return (leaf_stride / 32) * 8 + 33;  // skews up to 1 + (k - 1) <= 32
 }
 
 __host__ __device__ __forceinline__ size_t warp_smem_elems(int Q, int W, size_t leaf_stride) {
@@ -467,7 +472,7 @@ __device__ __forceinline__ void write_leaf_q(const T (&M)[RT], T C, const Plan& 
     }
 }
 
-// Stage leaf ell's record in shared memory, stg[stage_index(e, ell & 7)]; after
+// Stage leaf ell's record in shared memory, stg[8 e + (ell & 7) + skew(e)]; after
 // the eighth leaf of a group (the enumeration runs ell = 31 down to 0) write
 // the group out as 8-float runs, one full 32-byte sector per record element.
 template <typename T, int Q, int RT>
@@ -478,25 +483,26 @@ __device__ __forceinline__ void stage_leaf_q(const T (&M)[RT], T C, const Plan& 
     const int k = p.k, j = ell & 7;
     if (lane >= k && lane < p.m) {  // L column i: rows 0 .. i of the L block
         const int i = lane - k;
-        const int e0 = i * (i + 1) / 2;
+        T* sb = stg + 8 * (i * (i + 1) / 2) + j;  // skew 0
         sfor(std::make_integer_sequence<int, Q>{}, [&](auto rc) {
             constexpr int r = decltype(rc)::value;
-            if (r <= i) stg[stage_index(e0 + r, j)] = M[r];
+            if (r <= i) sb[8 * r] = M[r];
         });
     } else if (lane < k && ((carried_mask >> lane) & 1u)) {  // fixed variable in B
-        const int e0 = LQ + var_of_lane(p, lane) * (Q + 1);
+        const int v = var_of_lane(p, lane);
+        T* sb = stg + 8 * (LQ + v * (Q + 1)) + j + 1 + v;
         sfor(std::make_integer_sequence<int, Q>{}, [&](auto rc) {
             constexpr int r = decltype(rc)::value;
-            stg[stage_index(e0 + r, j)] = M[r];
+            sb[8 * r] = M[r];
         });
-        stg[stage_index(e0 + Q, j)] = C;
+        sb[8 * Q] = C;
     }
     if (j == 0) {  // the group ell .. ell + 7 is complete
         __syncwarp();
         const int R = (int)(p.leaf_stride / 32);
         for (int idx = lane; idx < R * 8; idx += 32) {
             const size_t ix = (size_t)(idx >> 3) * 32 + ell + (idx & 7);
-            if (GBN_IN(chk, 227, ix, p.leaf_stride)) rec[ix] = stg[stage_index(idx >> 3, idx & 7)];
+            if (GBN_IN(chk, 227, ix, p.leaf_stride)) rec[ix] = stg[idx + stage_skew<Q>(idx >> 3)];
         }
         __syncwarp();
     }
