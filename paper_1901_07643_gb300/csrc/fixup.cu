@@ -26,6 +26,8 @@ constexpr int kLdF = 33;
 __global__ void __launch_bounds__(1024) fix_flags_kernel(const Plan p, char* ws) {
     __shared__ float R[32 * kLdF];
     __shared__ float Ri[32 * kLdF];
+    grid_dep_wait();
+    grid_dep_launch();
     const int lane = threadIdx.x & 31, m = p.m;
     const double* R0 = reinterpret_cast<const double*>(ws + p.off_r0);
     {
@@ -62,6 +64,8 @@ constexpr int kScanBlocksPerChild = 64;
 
 // List the families of flagged children whose score is below the threshold.
 __global__ void fix_scan_kernel(const Plan p, char* ws, const float* __restrict__ out) {
+    grid_dep_wait();
+    grid_dep_launch();
     const int c = blockIdx.y;
     const unsigned mask = *reinterpret_cast<const unsigned*>(ws + p.off_fix);
     if (!((mask >> c) & 1u)) return;
@@ -110,6 +114,7 @@ __global__ void __launch_bounds__(32 * kFixWarps) fixup_kernel(const Plan p, cha
     __shared__ double M[kFixWarps * 32 * kLdF];
     __shared__ int pos_of[32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, m = p.m;
+    grid_dep_wait();
     if (threadIdx.x < m) pos_of[p.order[threadIdx.x]] = threadIdx.x;
     __syncthreads();
     const unsigned listed = *reinterpret_cast<const unsigned*>(ws + p.off_status + kFixCountOffset);
@@ -159,14 +164,17 @@ __global__ void __launch_bounds__(32 * kFixWarps) fixup_kernel(const Plan p, cha
 }  // namespace
 
 int launch_fix_flags(const Plan& p, char* ws, cudaStream_t stream) {
-    fix_flags_kernel<<<1, 1024, 0, stream>>>(p, ws);
+    if (launch_dep(fix_flags_kernel, dim3(1), dim3(1024), 0, stream, p, ws) != cudaSuccess)
+        return GBN_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 
 int launch_fixup(const Plan& p, char* ws, void* out, cudaStream_t stream) {
-    fix_scan_kernel<<<dim3(kScanBlocksPerChild, p.m), 256, 0, stream>>>(p, ws,
-                                                                       static_cast<float*>(out));
-    fixup_kernel<<<304, 32 * kFixWarps, 0, stream>>>(p, ws, static_cast<float*>(out));
+    if (launch_dep(fix_scan_kernel, dim3(kScanBlocksPerChild, p.m), dim3(256), 0, stream, p, ws,
+                   static_cast<const float*>(out)) != cudaSuccess ||
+        launch_dep(fixup_kernel, dim3(304), dim3(32 * kFixWarps), 0, stream, p, ws,
+                   static_cast<float*>(out)) != cudaSuccess)
+        return GBN_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 

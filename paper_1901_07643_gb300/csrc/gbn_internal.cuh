@@ -128,6 +128,32 @@ struct BatchView {
 
 // Dataset index for global block bx: the launch position l with
 // prefix[l] <= bx < prefix[l+1]; local = bx - prefix[l].
+// Programmatic dependent launch.  A kernel launched with launch_dep may be
+// dispatched while the previous kernel on the stream finishes; every such
+// kernel calls grid_dep_wait() before anything else, which returns once the
+// previous kernel has completed and its writes are visible, so results are
+// those of plain stream order (without such a launch the wait is a no-op).
+// grid_dep_launch() lets the next kernel be dispatched before this one ends.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t stream, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 __device__ __forceinline__ int batch_locate(const BatchView& v, const int64_t* prefix, int64_t bx,
                                             int64_t& local) {
     int lo = 0, hi = v.B;

@@ -317,19 +317,26 @@ __global__ void colsum_kernel(const Plan p, const double* __restrict__ X, char* 
     colsum_body(blockIdx.x, X, p.n, p.m, p.rows_per_panel, q.colsum, p.panels, q.chk);
 }
 __global__ void __launch_bounds__(kRedThreads) mean_kernel(const Plan p, char* ws) {
+    grid_dep_wait();
+    grid_dep_launch();
     const R0Ptrs q = r0_ptrs(p, ws);
     mean_body(q.colsum, p.panels, p.m, p.n, p.center, p, q.mu, q.chk);
 }
 __global__ void gram_kernel(const Plan p, const double* __restrict__ X, char* ws, int pass) {
+    grid_dep_wait();
     const R0Ptrs q = r0_ptrs(p, ws);
     gram_body(blockIdx.x, X, p.n, p.m, p.rows_per_panel, q.mu, p.panels, pass ? q.r1inv : nullptr,
               p, q.gram, q.chk);
 }
 __global__ void __launch_bounds__(kRedThreads) gram_sum_kernel(const Plan p, char* ws) {
+    grid_dep_wait();
+    grid_dep_launch();
     const R0Ptrs q = r0_ptrs(p, ws);
     gram_sum_body(blockIdx.x, q.gram, p.panels, p.m, q.gsum, q.chk);
 }
 __global__ void __launch_bounds__(kCholThreads) chol_kernel(const Plan p, char* ws, int pass) {
+    grid_dep_wait();
+    grid_dep_launch();
     const R0Ptrs q = r0_ptrs(p, ws);
     if (pass)
         chol_body(q.gsum, p.m, q.r1, q.r0, nullptr, q.status, q.chk);
@@ -388,14 +395,17 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel_b(const BatchView v,
 int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream) {
     if (cudaMemsetAsync(ws + p.off_status, 0, 256, stream) != cudaSuccess) return GBN_ERR_CUDA;
     if (p.center) colsum_kernel<<<p.panels, 256, 0, stream>>>(p, X, ws);
-    mean_kernel<<<1, kRedThreads, 0, stream>>>(p, ws);
     const unsigned groups = (unsigned)((p.m * (p.m + 1) / 2 + 31) / 32);
-    gram_kernel<<<p.panels, 512, 0, stream>>>(p, X, ws, 0);
-    gram_sum_kernel<<<groups, kRedThreads, 0, stream>>>(p, ws);
-    chol_kernel<<<1, kCholThreads, 0, stream>>>(p, ws, 0);
-    gram_kernel<<<p.panels, 512, 0, stream>>>(p, X, ws, 1);
-    gram_sum_kernel<<<groups, kRedThreads, 0, stream>>>(p, ws);
-    chol_kernel<<<1, kCholThreads, 0, stream>>>(p, ws, 1);
+    const cudaError_t e[] = {
+        launch_dep(mean_kernel, dim3(1), dim3(kRedThreads), 0, stream, p, ws),
+        launch_dep(gram_kernel, dim3(p.panels), dim3(512), 0, stream, p, X, ws, 0),
+        launch_dep(gram_sum_kernel, dim3(groups), dim3(kRedThreads), 0, stream, p, ws),
+        launch_dep(chol_kernel, dim3(1), dim3(kCholThreads), 0, stream, p, ws, 0),
+        launch_dep(gram_kernel, dim3(p.panels), dim3(512), 0, stream, p, X, ws, 1),
+        launch_dep(gram_sum_kernel, dim3(groups), dim3(kRedThreads), 0, stream, p, ws),
+        launch_dep(chol_kernel, dim3(1), dim3(kCholThreads), 0, stream, p, ws, 1)};
+    for (cudaError_t x : e)
+        if (x != cudaSuccess) return GBN_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
 }
 

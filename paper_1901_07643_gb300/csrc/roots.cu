@@ -668,6 +668,7 @@ __device__ __forceinline__ T* top_nodes(const Plan& p, char* ws) {
 template <typename T>
 __global__ void __launch_bounds__(32 * kTopDfsWarps) roots_top_dfs_kernel(const Plan p, char* ws) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    grid_dep_wait();
     const int warp = threadIdx.x >> 5;
     const uint64_t g = (uint64_t)blockIdx.x * kTopDfsWarps + warp;
     const uint64_t groups = (uint64_t)p.n_cta >> top_dfs_levels(p);
@@ -685,6 +686,7 @@ template <typename T, int QF>
 __global__ void __launch_bounds__(32 * kDfsWarps, (std::is_same<T, float>::value && QF > 0) ? 6 : 1)
     roots_leaves_kernel(const Plan p, char* ws) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    grid_dep_wait();
     const int warp = threadIdx.x >> 5;
     constexpr bool kReg = std::is_same<T, float>::value && QF > 0;
     constexpr int kWarpsPerCta = kReg ? 2 : 1;
@@ -743,7 +745,9 @@ int launch_leaves_q(const Plan& p, char* ws, size_t smem, cudaStream_t stream) {
         return GBN_ERR_CUDA;
     const int warps_per_cta = (std::is_same<T, float>::value && QF > 0) ? 2 : 1;
     const unsigned nb = (unsigned)((p.n_cta * warps_per_cta + kDfsWarps - 1) / kDfsWarps);
-    roots_leaves_kernel<T, QF><<<nb, 32 * kDfsWarps, smem, stream>>>(p, ws);
+    if (launch_dep(roots_leaves_kernel<T, QF>, dim3(nb), dim3(32 * kDfsWarps), smem, stream, p, ws) !=
+        cudaSuccess)
+        return GBN_ERR_CUDA;
     return GBN_OK;
 }
 
@@ -758,7 +762,9 @@ int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
     if (cudaFuncSetAttribute(roots_top_dfs_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_top) != cudaSuccess)
         return GBN_ERR_CUDA;
-    roots_top_dfs_kernel<T><<<nb_top, 32 * kTopDfsWarps, smem_top, stream>>>(p, ws);
+    if (launch_dep(roots_top_dfs_kernel<T>, dim3(nb_top), dim3(32 * kTopDfsWarps), smem_top, stream,
+                   p, ws) != cudaSuccess)
+        return GBN_ERR_CUDA;
     int rc;
     switch (p.W == 5 ? p.Q : 0) {
         case 4: rc = launch_leaves_q<T, 4>(p, ws, smem, stream); break;
