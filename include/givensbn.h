@@ -12,7 +12,10 @@
  *
  * at table slot idx(c,S) = c * 2^(m-1) + compress(S, c), where compress
  * deletes bit c from the m-bit parent mask (child-major table, one
- * (m-1)-bit parent mask per child).  RSS == 0 (exact collinearity) gives -inf.
+ * (m-1)-bit parent mask per child).  RSS == 0 (exact collinearity) gives -inf;
+ * in the FP32 walk so does an RSS below 2^-126 (the logarithm flushes
+ * subnormal inputs), and with opts.fixup_tau > 0 such families are listed
+ * and re-scored in FP64 (GBN_STATUS_FIXUP_OVERFLOW if the list overflows).
  *
  * How: one FP64 QR R0 of the centred n x m data (CholeskyQR2), then the
  * greedy sequence of adjacent column transpositions of Algorithm 1, each

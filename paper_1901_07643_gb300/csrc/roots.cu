@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(32 * kTopDfsWarps) roots_top_dfs_kernel(const 
 // with the stack in registers, FP64 in shared memory), or 0 for the generic
 // one; each instance gets the registers its own Q needs.
 template <typename T, int QF>
-__global__ void __launch_bounds__(32 * kDfsWarps, (std::is_same<T, float>::value && QF > 0) ? 6 : 1)
+__global__ void __launch_bounds__(32 * kDfsWarps, (std::is_same<T, float>::value && QF > 0) ? 7 : 1)
     roots_leaves_kernel(const Plan p, char* ws) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     grid_dep_wait();
@@ -783,7 +783,7 @@ int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
 // register-stack leaf enumeration of the single-dataset kernel, warps finding
 // their dataset through the prefix of walk CTAs.
 template <typename T, int QF>
-__global__ void __launch_bounds__(32 * kDfsWarps, 6)
+__global__ void __launch_bounds__(32 * kDfsWarps, 7)
     roots_leaves_kernel_bq(const BatchView v, size_t max_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
