@@ -518,6 +518,7 @@ struct Dfs5 {
                                                int topk, int ell, T* stack, const Plan& p, T* rec,
                                                unsigned long long* chk) {
         if constexpr (L == W) {
+            (void)rows;  // a leaf: no node below it
             stage_leaf_q<T, Q, RT>(M, C, p, lane, carried, ell, stack + stack_off<RT, W>(), rec,
                                    chk);
         } else {
@@ -570,6 +571,7 @@ struct Dfs5R {
                                                int topk, int ell, T* stg, const Plan& p, T* rec,
                                                unsigned long long* chk) {
         if constexpr (L == W) {
+            (void)rows;  // a leaf: no node below it
             stage_leaf_q<T, Q, RT>(M, C, p, lane, carried, ell, stg, rec, chk);
         } else {
             T sv[rows];
