@@ -38,12 +38,13 @@
 // consecutive table slots.
 //
 // FP32 scores with full warps of sub-walks take one of two refinements:
-//   * the paired walk: one block runs the sub-walks of two neighbouring roots
-//     CTAs (front sets differing in fixed variable W).  Two producer warps
-//     write one interleaved tape (c0, c1, s0, s1); a consumer lane holds a
-//     column of both sub-walks in float2 registers and rotates, sums and
-//     scores them with packed FP32 instructions, so the walk issues about
-//     16 instead of 24 instructions per family;
+//   * the paired walk: one block runs the 64 sub-walks of two neighbouring
+//     roots CTAs, and a consumer lane carries two of them whose front sets
+//     differ in fixed variable 0 only.  Two producer warps write one tape of
+//     (c_x, c_y, s_x, s_y) per step and lane; the lane holds its column of
+//     both sub-walks in float2 registers and rotates, sums and scores them
+//     with packed FP32 instructions, and both scores leave in one 8-byte
+//     store (the slots are adjacent);
 //   * the paired ring (Q <= 6): the same pairs in persistent blocks with two
 //     tapes in shared memory, so one pair's tape is written while the
 //     consumers replay the previous one.
@@ -363,7 +364,7 @@ struct Smem {
     static constexpr size_t bytes = off_bar + (size_t)chunks * sizeof(uint64_t);
 };
 
-// Shared memory of the paired walk: a tape of (c0, c1, s0, s1) per step and
+// Shared memory of the paired walk: a tape of (c_x, c_y, s_x, s_y) per step and
 // lane (FP32), then the chunk barriers (two producer arrivals each).
 template <int Q>
 struct SmemP {
