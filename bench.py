@@ -389,6 +389,20 @@ def _extras(dev, flush, args):
     return out
 
 
+def _aggregate(total_ms, fam, steps, world, device):
+    """Whole-job throughput: every rank scores its own dataset (weak scaling),
+    the timed total is the maximum over ranks (all-reduce MAX on `device`, a
+    CUDA device under NCCL, the CPU under gloo), and the value counts the
+    families of all ranks.  Returns (total_ms, value)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * fam * steps / (total_ms / 1e3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -436,12 +450,7 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * fam * args.steps / (total_ms / 1e3)
+    total_ms, value = _aggregate(sum(step_ms), fam, args.steps, world, dev)
     walk_mean = statistics.mean(walk_ms)
     del out32, ws32
     torch.cuda.empty_cache()
