@@ -14,6 +14,7 @@ own dataset (seed + rank): weak scaling, no collective on the data path.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -55,6 +56,8 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-extras", action="store_true",
                     help="skip the batched-workload and adjoint legs")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="take the automatic (q, consumer warps) instead of timing the candidates")
     return ap.parse_args()
 
 
@@ -180,29 +183,67 @@ def _gpu_id(dev_index):
         return vis.split(",")[dev_index] if vis else str(dev_index)
 
 
-def _cpu_baseline(X, n, m, seconds):
-    """Oracle (direct FP64 Householder per family) on a bounded sample of the workload."""
+def _error_sample(X, m, count, seed=12345):
+    """Seeded random families plus families of each near-collinear column pair (child one
+    column of the pair, parents holding the other): the families the CPU baseline times and
+    the error statistics compare."""
+    rng = np.random.default_rng(seed)
+    child = rng.integers(0, m, count).astype(np.int64)
+    mask = rng.integers(0, 1 << m, count, dtype=np.int64).astype(np.uint64)
+    mask &= ~(np.uint64(1) << child.astype(np.uint64))
+    C = np.corrcoef(X, rowvar=False)
+    pairs = [(a, b) for a in range(m) for b in range(m) if a != b and abs(C[a, b]) > 0.99]
+    if pairs:
+        pick = rng.integers(0, len(pairs), count // 8)
+        cc = np.array([pairs[i][0] for i in pick], np.int64)
+        pp = np.array([pairs[i][1] for i in pick], np.uint64)
+        mm = rng.integers(0, 1 << m, len(pick), dtype=np.int64).astype(np.uint64)
+        mm = (mm & ~(np.uint64(1) << cc.astype(np.uint64))) | (np.uint64(1) << pp)
+        child = np.concatenate([child, cc])
+        mask = np.concatenate([mask, mm])
+    order = rng.permutation(len(child))  # a prefix of the sample is a sample too
+    return child[order].astype(np.int32), mask[order]
+
+
+def _slots(child, mask, m):
+    """Table slots idx(c,S) = c 2^(m-1) + compress(S, c) of the sampled families."""
+    c = child.astype(np.uint64)
+    low = mask & ((np.uint64(1) << c) - np.uint64(1))
+    high = (mask >> (c + np.uint64(1))) << c
+    return ((c << np.uint64(m - 1)) + (low | high)).astype(np.int64)
+
+
+def _cpu_baseline(X, n, m, seconds, gathered):  # noqa: C901
+    """Oracle (direct FP64 Householder per family) on a bounded sample of the workload,
+    and the GPU tables' errors against it on the same families (`gathered`: precision ->
+    the table's values at the sampled slots)."""
     import oracle
     cores = _cores()
-    rng = np.random.default_rng(12345)
-
-    def sample(count):
-        child = rng.integers(0, m, count).astype(np.int32)
-        mask = np.array([int(rng.integers(0, 1 << m)) & ~(1 << int(c)) for c in child], np.uint64)
-        return child, mask
-
-    c, k = sample(max(cores * 4, 32))
+    c, k = _error_sample(X, m, max(cores * 4, 32), seed=1)
     t0 = time.perf_counter()
     oracle.scores_sampled(X, c, k, nthreads=cores)
     dt = max(time.perf_counter() - t0, 1e-3)
     count = int(min(2_000_000, max(len(c), len(c) * seconds / dt)))
-    c, k = sample(count)
+    c, k = gathered["families"]
+    c, k = c[:count], k[:count]
     t0 = time.perf_counter()
-    oracle.scores_sampled(X, c, k, nthreads=cores)
+    _, ref = oracle.scores_sampled(X, c, k, nthreads=cores)
     dt = time.perf_counter() - t0
-    return {"value": count / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{count} random families of the m={m}, n={n} workload, direct FP64 "
-                      f"Householder QR per family, OpenMP over families; {dt:.1f} s"}
+    errors = {}
+    for name, got in gathered.items():
+        if name == "families":
+            continue
+        got = np.asarray(got[:len(ref)], np.float64)
+        d = got - ref
+        scaled = np.abs(d) / np.maximum(np.abs(ref), n)
+        errors[name] = {"max_scaled": float(scaled.max()),
+                        "max_rel_rss": float(np.max(np.abs(np.expm1(d / n)))),
+                        "count": int(len(ref)),
+                        "tolerance": 1e-4 if name == "fp32" else 1e-10}
+    return ({"value": len(ref) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+             "sample": f"{len(ref)} families of the m={m}, n={n} workload (seeded random, 1/9 "
+                       f"of them near-collinear-pair families), direct FP64 Householder QR per "
+                       f"family, OpenMP over families; {dt:.1f} s"}, errors)
 
 
 def run_reference(args):
@@ -268,7 +309,7 @@ def _time_steps(fn, steps, flush, stream):
     return step_ms, walk_ms
 
 
-def _e2e(X, Xd, fam, q32, w, world, dev, args):
+def _e2e(X, Xd, fam, q32, cw32, w, world, dev, args):
     """End to end through the public call: pinned host X copied in, the table
     delivered to pinned host memory, both inside the timed region.  Three ways
     of delivering the table are timed and the fastest is reported: a device
@@ -281,22 +322,24 @@ def _e2e(X, Xd, fam, q32, w, world, dev, args):
     outh = torch.empty(fam, dtype=torch.float32, pin_memory=True)
     Xd2 = torch.empty_like(Xd)
     outd = torch.empty(fam, dtype=torch.float32, device=dev)
-    wsd = torch.empty(binding.workspace_size(w.n, w.m, 0, q32), dtype=torch.uint8, device=dev)
+    wsd = torch.empty(binding.workspace_size(w.n, w.m, 0, q32, consumer_warps=cw32),
+                      dtype=torch.uint8, device=dev)
+    kw = dict(q=q32, consumer_warps=cw32, workspace=wsd, check=False)
 
     def via_copy():
         Xd2.copy_(Xh, non_blocking=True)
-        binding.score_all_families(Xd2, outd, q=q32, workspace=wsd, check=False)
+        binding.score_all_families(Xd2, outd, **kw)
         outh.copy_(outd, non_blocking=True)
 
     def direct():
         Xd2.copy_(Xh, non_blocking=True)
-        binding.score_all_families(Xd2, outh, q=q32, workspace=wsd, check=False)
+        binding.score_all_families(Xd2, outh, **kw)
 
     streams = [torch.cuda.Stream(dev) for _ in range(4)]
 
     def via_copy_streams():  # the table copied back as four concurrent chunks
         Xd2.copy_(Xh, non_blocking=True)
-        binding.score_all_families(Xd2, outd, q=q32, workspace=wsd, check=False)
+        binding.score_all_families(Xd2, outd, **kw)
         done = torch.cuda.Event()
         done.record()
         part = (fam + len(streams) - 1) // len(streams)
@@ -343,16 +386,23 @@ def _extras(dev, flush, args):
     out = {}
     Xs = [torch.from_numpy(X).to(dev) for X in synthetic.batched_bootstrap()]
     offs, total = binding.batch_offsets(Xs)
+    q, cw, tune = 0, 0, None
+    if not args.no_autotune:
+        q, cw, ms, table = binding.autotune_batched(Xs)
+        tune = {"q": q, "consumer_warps": cw, "median_ms": ms,
+                "candidates": [{"q": a, "consumer_warps": b, "median_ms": t} for a, b, t in table]}
+        torch.cuda.empty_cache()
+    kw = dict(q=q, consumer_warps=cw)
     tbl = torch.empty(total, dtype=torch.float32, device=dev)
-    ws = torch.empty(binding.batched_workspace_size(Xs), dtype=torch.uint8, device=dev)
+    ws = torch.empty(binding.batched_workspace_size(Xs, **kw), dtype=torch.uint8, device=dev)
     for _ in range(2):
-        binding.score_all_families_batched(Xs, tbl, workspace=ws)
+        binding.score_all_families_batched(Xs, tbl, workspace=ws, **kw)
     graph = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream(dev)
     s.wait_stream(torch.cuda.current_stream(dev))
     with torch.cuda.stream(s):
         with torch.cuda.graph(graph, stream=s):
-            binding.score_all_families_batched(Xs, tbl, workspace=ws)
+            binding.score_all_families_batched(Xs, tbl, workspace=ws, **kw)
     torch.cuda.current_stream(dev).wait_stream(s)
     ms = []
     for _ in range(max(3, args.steps // 2)):
@@ -366,7 +416,8 @@ def _extras(dev, flush, args):
     t = statistics.median(ms)
     out["batched"] = {"workload": "bootstrap_256 (m~U{12..20}, n~U{100..5000})", "datasets": len(Xs),
                       "families": total, "ms_per_batch": t, "value": total / (t / 1e3),
-                      "unit": UNIT, "launch": "one captured CUDA graph"}
+                      "unit": UNIT, "launch": "one captured CUDA graph",
+                      "q": q or None, "consumer_warps": cw or None, "autotune": tune}
     del tbl, ws, graph
     Gs, w = synthetic.gradient_workload()
     Gd = [torch.from_numpy(X).to(dev) for X in Gs]
@@ -387,6 +438,48 @@ def _extras(dev, flush, args):
                       "ms_total": t, "value": fam / (t / 1e3), "unit": "family adjoints/s",
                       "dtype": "f32 walk, f64 accumulation"}
     return out
+
+
+def _search_leg(table, m, flush, args):
+    """Exact structure search (best parents + subset dynamic programme) over the FP32 table
+    just scored, timed with CUDA events; the best-parent transform's algorithmic HBM bytes
+    (one read and one write of value + argmin per slot and pass) give its roofline."""
+    import torch
+    from paper_1901_07643_gb300 import binding
+    dev = table.device
+    b = ctypes.c_size_t(0)
+    binding.load().givensbn_structure_search_workspace_size(m, ctypes.byref(b))
+    ws = torch.empty(int(b.value), dtype=torch.uint8, device=dev)
+    parents, order, total = binding.structure_search(table, workspace=ws)  # warm-up
+    ms, ms_bp = [], []
+    best = torch.empty_like(table)
+    bset = torch.empty(table.numel(), dtype=torch.int32, device=dev)
+    for _ in range(3):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record()
+        binding.structure_search(table, workspace=ws)
+        e[1].record()
+        flush.zero_()
+        e[2].record()
+        binding.best_parents(table)
+        e[3].record()
+        torch.cuda.synchronize()
+        ms.append(e[0].elapsed_time(e[1]))
+        ms_bp.append(e[2].elapsed_time(e[3]))
+    del best, bset, ws
+    slots = m << (m - 1)
+    passes = 1 + -(-max(0, (m - 1) - 12) // 9)
+    bp_bytes = slots * (4 + 8) + (passes - 1) * slots * 16
+    t_bp = statistics.median(ms_bp)
+    peak, kind = _peak_hbm()
+    return {"workload": f"optimal DAG over the m={m} FP32 table", "ms": statistics.median(ms),
+            "best_parents_ms": t_bp, "best_parents_passes": passes,
+            "best_parents_roofline": {"bound": "hbm", "achieved": bp_bytes / (t_bp / 1e3) / 1e9,
+                                      "peak": peak, "unit": "GB/s",
+                                      "frac": bp_bytes / (t_bp / 1e3) / 1e9 / peak,
+                                      "algorithmic_bytes": bp_bytes, "peak_kind": kind},
+            "network_score": total, "edges": int(sum(bin(p).count("1") for p in parents))}
 
 
 def _aggregate(total_ms, fam, steps, world, device):
@@ -421,21 +514,38 @@ def run_ours(args):
     Xd = torch.from_numpy(X).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
+    tuned = {}
+
     def make(precision):
         q = args.q if (args.q and (precision == 0 or args.q <= 8)) else 0
+        cw = 0
+        if not q and not args.no_autotune:  # time the candidate plans, take the fastest
+            q, cw, ms, table = binding.autotune(Xd, precision=precision)
+            tuned["fp64" if precision else "fp32"] = {
+                "q": q, "consumer_warps": cw, "median_ms": ms,
+                "candidates": [{"q": a, "consumer_warps": b, "median_ms": t}
+                               for a, b, t in table]}
+            torch.cuda.empty_cache()
         out = torch.empty(fam, dtype=torch.float64 if precision else torch.float32, device=dev)
-        ws = torch.empty(binding.workspace_size(w.n, w.m, precision, q), dtype=torch.uint8,
-                         device=dev)
+        ws = torch.empty(binding.workspace_size(w.n, w.m, precision, q, consumer_warps=cw),
+                         dtype=torch.uint8, device=dev)
 
         def fn(ev):
-            binding.score_all_families(Xd, out, precision=precision, q=q, workspace=ws,
-                                       stage_events=ev, check=False)
-        return fn, out, ws, q
+            binding.score_all_families(Xd, out, precision=precision, q=q, consumer_warps=cw,
+                                       workspace=ws, stage_events=ev, check=False)
+        return fn, out, ws, q, cw
 
-    fn32, out32, ws32, q32 = make(0)
+    want_errors = rank == 0 and world == 1 and not args.skip_cpu_baseline
+    gathered = {}
+    if want_errors:
+        gathered["families"] = _error_sample(X, w.m, 1 << 18)
+        slots_t = torch.from_numpy(_slots(*gathered["families"], w.m)).to(dev)
+
+    fn32, out32, ws32, q32, cw32 = make(0)
     for _ in range(max(args.warmup, 0)):
         fn32([torch.cuda.Event(enable_timing=True) for _ in range(4)])
-    binding.score_all_families(Xd, out32, q=q32, workspace=ws32, check=True)  # status check
+    binding.score_all_families(Xd, out32, q=q32, consumer_warps=cw32, workspace=ws32,
+                               check=True)  # status check
     torch.cuda.synchronize()
     assert bool(torch.isfinite(out32).all()), "non-finite scores"
 
@@ -452,31 +562,37 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
     total_ms, value = _aggregate(sum(step_ms), fam, args.steps, world, dev)
     walk_mean = statistics.mean(walk_ms)
+    if want_errors:
+        gathered["fp32"] = out32[slots_t].double().cpu().numpy()
+    search_leg = None if args.skip_extras else _search_leg(out32, w.m, flush, args)
     del out32, ws32
     torch.cuda.empty_cache()
 
     fp64 = None
     if not args.skip_fp64:
-        fn64, out64, ws64, q64 = make(1)
+        fn64, out64, ws64, q64, cw64 = make(1)
         for _ in range(max(args.warmup, 1)):
             fn64([torch.cuda.Event(enable_timing=True) for _ in range(4)])
         k64 = max(3, args.steps // 2)
         s64, w64 = _time_steps(fn64, k64, flush, stream)
         fp64 = {"value": fam * k64 / (sum(s64) / 1e3), "ms_per_step": statistics.mean(s64),
-                "walk_ms": statistics.mean(w64), "q": binding.auto_q(w.m, 1) if not q64 else q64,
+                "walk_ms": statistics.mean(w64),
+                "q": q64 or binding.auto_q(w.m, 1), "consumer_warps": cw64 or None,
                 "dtype": "f64", "steps": k64}
+        if want_errors:
+            gathered["fp64"] = out64[slots_t].cpu().numpy()
         del out64, ws64
         torch.cuda.empty_cache()
 
     e2e = None
     if not args.skip_e2e:
-        e2e = _e2e(X, Xd, fam, q32, w, world, dev, args)
+        e2e = _e2e(X, Xd, fam, q32, cw32, w, world, dev, args)
 
     extras = {} if args.skip_extras else _extras(dev, flush, args)
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.skip_cpu_baseline:
-        cpu = _cpu_baseline(X, w.n, w.m, args.cpu_seconds)
+    cpu, errors = None, None
+    if want_errors:
+        cpu, errors = _cpu_baseline(X, w.n, w.m, args.cpu_seconds, gathered)
 
     peak, peak_kind = _peak_hbm()
     algo_bytes = 4 * fam  # the fp32 score table written once
@@ -486,7 +602,9 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "m": w.m, "n": w.n, "families": fam,
-                   "q": q32 or binding.auto_q(w.m, 0), "precision": "fp32 walk, fp64 CholeskyQR2 R0",
+                   "q": q32 or binding.auto_q(w.m, 0), "consumer_warps": cw32 or None,
+                   "plan": "autotuned (givensbn_autotune)" if tuned.get("fp32") else "fixed",
+                   "precision": "fp32 walk, fp64 CholeskyQR2 R0",
                    "l2": "256 MiB buffer zeroed between timed steps (> 129 MB L2); each step "
                          f"also writes a {fam * 4 / 1e9:.3g} GB table",
                    "parallelism": f"replicas x{world}, one dataset per GPU"},
@@ -498,11 +616,15 @@ def run_ours(args):
                      "peak_kind": peak_kind, "kernel": _walk_kernel_name(w.m, q32 or binding.auto_q(w.m, 0)),
                      "algorithmic_bytes_per_launch": algo_bytes},
         "cpu_baseline": cpu,
+        "errors": errors,
+        "autotune": tuned or None,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
     }
     line.update(extras)
+    if search_leg:
+        line["structure_search"] = search_leg
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

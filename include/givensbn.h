@@ -61,12 +61,17 @@ extern "C" {
 #define GBN_ERR_PRECISION (-8)  /* opts->precision not 0 or 1 */
 #define GBN_ERR_BATCH (-9)      /* batched arguments inconsistent */
 #define GBN_ERR_STATIC_SCRATCH (-10) /* input needs more than the no-alloc entry point's scratch */
+#define GBN_ERR_OPTS (-11)      /* an option outside its range (score, shard, consumer warps) */
+#define GBN_ERR_TUNE (-12)      /* the autotuner could not time or record a candidate */
 
 /* device status bits (givensbn_status) */
 #define GBN_STATUS_RANK_DEFICIENT 1 /* a Cholesky pivot was <= 0: RSS 0 for some families */
 #define GBN_STATUS_WATCHDOG 2       /* a bounded wait inside a kernel expired: output incomplete */
 #define GBN_STATUS_FIXUP_OVERFLOW 4 /* more ill-conditioned families than the fix-up list holds;
                                        the rest keep their FP32 scores */
+#define GBN_STATUS_BAD_FAMILY 8     /* givensbn_family_coefficients: a listed family was invalid
+                                       (child out of range, or parents holding the child or
+                                       variables >= m); its outputs are NaN */
 
 #define GBN_MIN_M 2
 #define GBN_MAX_M 30
@@ -85,9 +90,30 @@ typedef struct givensbn_opts {
     double fixup_tau;       /* FP32 walk only: a family whose RSS falls below fixup_tau times
                                the child's centred sum of squares is recomputed in FP64 from R0
                                (QR of its columns) and scored in FP64; 0 disables.  Default 1e-6 */
+    int64_t watchdog_ns;    /* bound, in nanoseconds, on every wait between the warps of a walk
+                               block; on expiry the kernel sets GBN_STATUS_WATCHDOG and returns
+                               (the table is then incomplete).  0 = the default, 2 s */
+    int32_t max_parents;    /* bounded in-degree K: only families with |S| <= K are written (the
+                               other slots of the table are left untouched); -1 = no bound
+                               (default) */
+    int32_t score;          /* GBN_SCORE_BIC (default), GBN_SCORE_AIC or GBN_SCORE_PENALTY */
+    double penalty;         /* GBN_SCORE_PENALTY: score = n ln(RSS/n) + penalty * |S| */
+    int32_t shard_index;    /* score only shard shard_index of shard_count shards of the table */
+    int32_t shard_count;    /* (see givensbn_shard_range); 0 or 1 = the whole table (default) */
+    int32_t consumer_warps; /* consumer warps per walk block, 1..8; 0 = automatic */
+    int32_t reserved0;
+    const char* tune_cache; /* host path of an autotuner cache file (givensbn_autotune), or NULL.
+                               With q == 0 and consumer_warps == 0 the plan takes the cached
+                               choice for this device and size class, else the automatic one */
 } givensbn_opts;
 
-/* Default options: FP32, centring on, automatic q, no workspace, fixup_tau 1e-6. */
+/* Score of a family from its residual sum of squares (opts->score). */
+#define GBN_SCORE_BIC 0     /* n ln(RSS/n) + |S| ln n */
+#define GBN_SCORE_AIC 1     /* n ln(RSS/n) + 2 |S| */
+#define GBN_SCORE_PENALTY 2 /* n ln(RSS/n) + opts->penalty * |S| */
+
+/* Default options: FP32, centring on, automatic q, no workspace, fixup_tau 1e-6, BIC score, no
+ * in-degree bound, the whole table, the default watchdog, no tuning cache. */
 void givensbn_default_opts(givensbn_opts* opts);
 
 /*
@@ -120,6 +146,28 @@ const char* givensbn_strerror(int code);
 
 /* The q the automatic choice picks for (m, precision). */
 int32_t givensbn_auto_q(int32_t m, int32_t precision);
+
+/* The sub-walk size q and consumer warps per walk block that a call with these arguments
+ * would use (opts->q / opts->consumer_warps, else the tuning cache, else the automatic
+ * choice).  Host only; no device work.  Returns 0 or GBN_ERR_*. */
+int givensbn_plan_choice(int64_t n, int32_t m, const givensbn_opts* opts, int32_t* q,
+                         int32_t* consumer_warps);
+
+/*
+ * Sharding one table (the parallel split of Sec. 6, Algorithm 2, across calls).
+ * The walk runs 2^k sub-walks, k = m - q, one per front set F of the fixed variables
+ * H = {0 .. k-1}; sub-walk F writes exactly the families (c, S) with S n H = F.  The
+ * sub-walks are grouped 2^W to a CTA (W = min(5, k), lanes over the lowest W fixed
+ * variables), CTA g holding the front sets with F >> W == g.  With
+ * opts->shard_count = N > 1, the call with shard_index = i walks only CTAs
+ * [cta_begin, cta_end) (contiguous ranges of CTA pairs, one per shard, covering all
+ * 2^(k-W) CTAs once), i.e. it writes exactly the families with
+ * ((S & (2^k - 1)) >> W) in [cta_begin, cta_end) and leaves every other slot of
+ * out_scores untouched.  Shards need no communication; every shard computes R0 itself.
+ * This call reports k, W and the range for (n, m, opts).  Host only.  Returns 0 or
+ * GBN_ERR_*. */
+int givensbn_shard_range(int64_t n, int32_t m, const givensbn_opts* opts, int32_t* fixed_k,
+                         int32_t* lane_bits, int64_t* cta_begin, int64_t* cta_end);
 
 /*
  * Scores of B datasets of uneven size in one set of launches (the same
@@ -192,11 +240,127 @@ int givensbn_backward_workspace_size(int64_t n, int32_t m, const givensbn_opts* 
  * All calls on a device share that scratch, so calls must not overlap: a
  * call may start only after the previous call's kernels have completed.  The
  * first call on each device looks up the scratch address (with that device
- * current); make it before any stream capture.  Device status words are not
+ * current); make it before any stream capture.  The address is kept for the
+ * life of the process, so after cudaDeviceReset of a device this entry point
+ * must not be called on that device again.  Device status words are not
  * reported by this entry point.  Returns 0 or GBN_ERR_*.
  */
 int score_all_families_noalloc(const double* X, int64_t n, int32_t m, float* out_scores,
                                void* stream);
+
+/*
+ * Autotuner (the split size of Sec. 6 / Algorithm 2 and the walk block's consumer warps,
+ * measured on the device).  Times whole scoring calls for the candidates q in
+ * {a-1, a, a+1} (a = the automatic choice; within the compiled range and <= m) times
+ * consumer warps in {4, 6, 8}: one untimed call, then the median of three calls timed with
+ * CUDA events on opts->stream (the call synchronises that stream).  The fastest candidate
+ * is returned and, when opts->tune_cache is set, appended to that file as one line
+ *   gbn-tune-v1 device=<name> kind=single precision=<p> m=<m> mmin=<m> count=1
+ *               nlog2=<floor(log2 n)> q=<q> cw=<warps> ms=<median ms>
+ * Later calls with q == 0, consumer_warps == 0 and the same tune_cache take the last line
+ * matching their device (or device=*), kind, precision, m, mmin, count and nlog2.
+ *   X, out_scores  as for score_all_families (out_scores is overwritten by the trials)
+ *   opts           host; workspace >= givensbn_autotune_workspace_size(); opts->q and
+ *                  opts->consumer_warps are ignored (they are what is tuned)
+ *   q_out, cw_out, ms_out   host, may be NULL: the winner and its median time
+ *   results        host array of max_results entries, may be NULL: every candidate's time
+ *   n_results      host, may be NULL: the number of candidates timed
+ * Returns 0, GBN_ERR_* of a trial call, or GBN_ERR_TUNE if the cache file cannot be
+ * written (the winner is still returned).
+ */
+typedef struct givensbn_tune_result {
+    int32_t q;
+    int32_t consumer_warps;
+    double ms;
+} givensbn_tune_result;
+
+int givensbn_autotune_workspace_size(int64_t n, int32_t m, const givensbn_opts* opts,
+                                     size_t* bytes);
+int givensbn_autotune(const double* X, int64_t n, int32_t m, void* out_scores,
+                      const givensbn_opts* opts, int32_t* q_out, int32_t* cw_out, double* ms_out,
+                      givensbn_tune_result* results, int32_t max_results, int32_t* n_results);
+
+/* The same for score_all_families_batched: one common q for the batch (candidates around
+ * the smallest automatic choice, q <= the smallest m), cached as kind=batch with m = the
+ * largest m, mmin = the smallest, count = B and nlog2 = floor(log2(sum of n)). */
+int givensbn_autotune_batched_workspace_size(const int64_t* ns, const int32_t* ms, int32_t B,
+                                             const givensbn_opts* opts, size_t* bytes);
+int givensbn_autotune_batched(const double* const* Xs, const int64_t* ns, const int32_t* ms,
+                              int32_t B, void* out, const int64_t* out_offsets,
+                              const givensbn_opts* opts, int32_t* q_out, int32_t* cw_out,
+                              double* ms_out, givensbn_tune_result* results, int32_t max_results,
+                              int32_t* n_results);
+
+/*
+ * Least-squares coefficients of listed families (the regression of Sec. 1.1, solved on the
+ * initial QR decomposition R0 of Sec. 2 instead of the n x m data: Xc = Q R0 gives the same
+ * problem with m rows).  FP64 throughout: R0 by CholeskyQR2, then per family Householder QR
+ * of R0's columns for S and c, the residual sum of squares and back substitution.
+ *   X        device, n x m FP64 row-major (centred by the call unless opts->center == 0)
+ *   child    device, count int32 child variables
+ *   parents  device, count uint64 parent bitmasks (bit v = variable v; must not hold the
+ *            child or bits >= m)
+ *   beta     device, count x (m + 1) doubles, written: row f holds b_v for v in S at index
+ *            v, 0 for the other variables, and at index m the intercept
+ *            mean_c - sum_v b_v mean_v (0 when opts->center == 0)
+ *   rss      device, count doubles (RSS of each family), or NULL
+ *   opts     host; precision and q are ignored; workspace >=
+ *            givensbn_coefficients_workspace_size()
+ * An invalid family gets NaN outputs and sets GBN_STATUS_BAD_FAMILY; a family whose parent
+ * columns are linearly dependent gets NaN coefficients (its RSS is still written) and sets
+ * GBN_STATUS_RANK_DEFICIENT (givensbn_status).  Returns 0 or GBN_ERR_*.
+ */
+int givensbn_coefficients_workspace_size(int64_t n, int32_t m, const givensbn_opts* opts,
+                                         size_t* bytes);
+int givensbn_family_coefficients(const double* X, int64_t n, int32_t m, const int32_t* child,
+                                 const uint64_t* parents, int64_t count, double* beta,
+                                 double* rss, const givensbn_opts* opts);
+
+/*
+ * Exact structure search over a local-score table (the use of the all-family scores that the
+ * method serves, Sec. 1: learning a Bayesian network structure from every child / parent-set
+ * score).  Lower scores are better; a slot holding +inf is a family that may not be chosen
+ * (e.g. |S| > K after a bounded-in-degree call, if the caller filled the table with +inf
+ * first).  The search finds a DAG minimising sum_c score(c, parents(c)):
+ *   1. best parents: B[c][U] = min over S subset of U of score(c, S) and its argmin, for every
+ *      child c and candidate set U of the other variables (a subset-minimum transform);
+ *   2. F[W] = min over c in W of F[W \ c] + B[c][W \ c], F[{}] = 0, over all 2^m subsets
+ *      W in order of size (FP64 sums); c is the sink of W;
+ *   3. backtracking from W = all variables through the sinks.
+ * Ties go to the smaller parent set in step 1 and to the smallest sink in step 2.
+ *
+ * givensbn_best_parents: step 1 alone.
+ *   scores    device, m * 2^(m-1) floats in table layout (see score_all_families)
+ *   best      device, m * 2^(m-1) floats, written: best[c 2^(m-1) + u] = B[c][U] for the
+ *             compressed candidate mask u of U (the table's own slot indexing)
+ *   best_set  device, m * 2^(m-1) uint32, written: the compressed mask of the argmin S
+ *   opts      host, may be NULL (stream only)
+ * givensbn_structure_search: all three steps.
+ *   scores    as above
+ *   parents   device, m uint32, written: the parent bitmask (bit v = variable v) of each
+ *             variable in an optimal DAG
+ *   order     device, m int32, or NULL: an optimal variable ordering (parents come first)
+ *   total     device, one double: the optimal network score (the FP64 sum of the chosen
+ *             table entries)
+ *   opts      host; workspace >= givensbn_structure_search_workspace_size(m) (8 bytes per
+ *             table slot plus 9 bytes per variable subset; 7.3 GB at m = 26)
+ * Both are asynchronous on opts->stream and return 0 or GBN_ERR_*.
+ */
+int givensbn_best_parents(const float* scores, int32_t m, float* best, uint32_t* best_set,
+                          const givensbn_opts* opts);
+
+/*
+ * Measured arithmetic-pipe peaks of the current device (a measurement helper, not part of
+ * the paper's method): FP32 and FP64 fused multiply-add throughput in TFLOP/s (2 flops per
+ * FMA), each the best of three timed launches of independent FMA chains on every SM.
+ *   scratch  device, 8 bytes, 8-byte aligned (never written for these inputs)
+ *   stream   cudaStream_t (synchronised)
+ * Returns 0 or GBN_ERR_*.
+ */
+int givensbn_pipe_peaks(void* scratch, void* stream, double* fp32_tflops, double* fp64_tflops);
+int givensbn_structure_search_workspace_size(int32_t m, size_t* bytes);
+int givensbn_structure_search(const float* scores, int32_t m, uint32_t* parents, int32_t* order,
+                              double* total, const givensbn_opts* opts);
 
 #ifdef __cplusplus
 }

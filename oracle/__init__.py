@@ -57,6 +57,10 @@ def _load():
             lib.oracle_set_mutation.argtypes = [ctypes.c_int]
             lib.oracle_num_threads.argtypes = [ctypes.c_int]
             lib.oracle_num_threads.restype = ctypes.c_int
+            lib.oracle_table_scores.argtypes = [d, i64, i32, ctypes.c_double, d]
+            lib.oracle_scores_sampled_reduced.argtypes = [d, i64, i32, d, d, i64, d, d,
+                                                          ctypes.c_int]
+            lib.oracle_coefficients.argtypes = [d, i64, i32, d, d, i64, d, d, ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -82,8 +86,11 @@ def compress(S: int, c: int) -> int:
     return int(_load().oracle_compress(S, c))
 
 
-def scores(X, nthreads: int = 0, reduced: bool = False):
-    """(rss, score) tables of every family, each m*2^(m-1) FP64 in table layout."""
+def scores(X, nthreads: int = 0, reduced: bool = False, penalty=None):
+    """(rss, score) tables of every family, each m*2^(m-1) FP64 in table layout.
+
+    The score is n ln(RSS/n) + |S| * penalty, penalty = ln n (BIC) by default.
+    """
     X = _f64(X)
     n, m = X.shape
     rss = np.empty(m << (m - 1), np.float64)
@@ -91,19 +98,38 @@ def scores(X, nthreads: int = 0, reduced: bool = False):
     fn = _load().oracle_scores_reduced if reduced else _load().oracle_scores
     if fn(_ptr(X), n, m, _ptr(rss), _ptr(sc), nthreads) != 0:
         raise ValueError("oracle: invalid shape")
+    if penalty is not None:
+        _load().oracle_table_scores(_ptr(rss), n, m, float(penalty), _ptr(sc))
     return rss, sc
 
 
-def scores_sampled(X, child, mask, nthreads: int = 0):
-    """(rss, score) of the listed families (child[i], parent bitmask[i]), direct on Xc."""
+def coefficients(X, child, mask, nthreads: int = 0):
+    """(beta, rss) of the listed families, directly on Xc: beta is count x (m+1)
+    (b_v at column v for v in the parent set, 0 elsewhere, intercept in column m)."""
+    X = _f64(X)
+    n, m = X.shape
+    child = np.ascontiguousarray(child, dtype=np.int32)
+    mask = np.ascontiguousarray(mask, dtype=np.uint64)
+    beta = np.empty((len(child), m + 1), np.float64)
+    rss = np.empty(len(child), np.float64)
+    if _load().oracle_coefficients(_ptr(X), n, m, _ptr(child), _ptr(mask), len(child),
+                                   _ptr(beta), _ptr(rss), nthreads) != 0:
+        raise ValueError("oracle: invalid shape")
+    return beta, rss
+
+
+def scores_sampled(X, child, mask, nthreads: int = 0, reduced: bool = False):
+    """(rss, score) of the listed families (child[i], parent bitmask[i]), direct on Xc
+    (or, reduced=True, on the oracle's own Householder R0 of Xc)."""
     X = _f64(X)
     n, m = X.shape
     child = np.ascontiguousarray(child, dtype=np.int32)
     mask = np.ascontiguousarray(mask, dtype=np.uint64)
     rss = np.empty(len(child), np.float64)
     sc = np.empty_like(rss)
-    if _load().oracle_scores_sampled(_ptr(X), n, m, _ptr(child), _ptr(mask), len(child),
-                                     _ptr(rss), _ptr(sc), nthreads) != 0:
+    fn = _load().oracle_scores_sampled_reduced if reduced else _load().oracle_scores_sampled
+    if fn(_ptr(X), n, m, _ptr(child), _ptr(mask), len(child), _ptr(rss), _ptr(sc),
+          nthreads) != 0:
         raise ValueError("oracle: invalid shape")
     return rss, sc
 

@@ -130,11 +130,16 @@ double oracle_family_rss(const double* A, int64_t rows, int32_t m, int32_t c, ui
     return rss;
 }
 
-double oracle_bic(double rss, int64_t n, int32_t k) {
+/* Penalised local score n*ln(RSS/n) + k*lam: lam = ln(n) is the BIC-style
+ * score of the benchmark configurations, lam = 2 the AIC form (the paper
+ * leaves the score open, Sec. 1; only the RSS is the method's result). */
+double oracle_score(double rss, int64_t n, int32_t k, double lam) {
     double pen = (double)k;
     if (g_mutation == 5) pen = (double)(k + 1); /* planted: penalty off by one */
-    return (double)n * log(rss / (double)n) + pen * log((double)n);
+    return (double)n * log(rss / (double)n) + pen * lam;
 }
+
+double oracle_bic(double rss, int64_t n, int32_t k) { return oracle_score(rss, n, k, log((double)n)); }
 
 /* Householder R factor (m x m, row-major, upper triangular) of row-major A. */
 void oracle_r_factor(const double* A, int64_t rows, int32_t m, double* R) {
@@ -185,6 +190,90 @@ static void all_families(const double* A, int64_t rows, int32_t m, int64_t n, do
     }
 }
 
+/* Scores with penalty lam per parent from a table of RSS in table layout. */
+void oracle_table_scores(const double* rss, int64_t n, int32_t m, double lam, double* score) {
+    const int64_t half = 1ll << (m - 1);
+    for (int64_t f = 0; f < (int64_t)m * half; ++f)
+        score[f] = oracle_score(rss[f], n, popcount64((uint64_t)(f % half)), lam);
+}
+
+/*
+ * Least-squares coefficients of listed families, directly on the centred data
+ * (Sec. 1.1: the regression of child[i] on the parents in mask[i]): Householder
+ * QR of [Xc_S | Xc_c], then back substitution R b = (Q^T y)(0:k).  beta holds
+ * m + 1 doubles per family: b_v at index v for v in S, 0 elsewhere, and the
+ * intercept mean_c - sum_v b_v mean_v of the uncentred regression at index m.
+ * Numerically dependent parents -- a pivot |r_jj| (parent j's residual on the
+ * parents before it) at most 1e-12 times the norm of parent j's column --
+ * give NaN coefficients; the RSS is still returned.
+ */
+int oracle_coefficients(const double* X, int64_t n, int32_t m, const int32_t* child,
+                        const uint64_t* mask, int64_t count, double* beta, double* rss_out,
+                        int nthreads) {
+    if (m < 1 || m > 30 || n < 1) return -1;
+    double* Xc = (double*)malloc(sizeof(double) * (size_t)n * (size_t)m);
+    double mu[32];
+    oracle_center(X, n, m, Xc);
+    for (int32_t j = 0; j < m; ++j) { /* the column means, summed as in oracle_center */
+        double s = 0.0;
+        for (int64_t t = 0; t < n; ++t) s += X[t * m + j];
+        mu[j] = s / (double)n;
+    }
+#ifdef _OPENMP
+#pragma omp parallel num_threads(oracle_num_threads(nthreads))
+#endif
+    {
+        double* work = (double*)malloc(sizeof(double) * (size_t)n * (size_t)(m + 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 16)
+#endif
+        for (int64_t i = 0; i < count; ++i) {
+            const int32_t c = child[i];
+            const uint64_t S = mask[i];
+            double* b = beta + i * (int64_t)(m + 1);
+            int32_t cols[32];
+            double bk[32], norm[32];
+            int32_t k = 0;
+            for (int32_t v = 0; v < m; ++v) {
+                b[v] = 0.0;
+                if (!((S >> v) & 1ull)) continue;
+                cols[k] = v;
+                double s2 = 0.0;
+                for (int64_t t = 0; t < n; ++t) {
+                    work[(int64_t)k * n + t] = Xc[t * m + v];
+                    s2 += Xc[t * m + v] * Xc[t * m + v];
+                }
+                norm[k] = sqrt(s2);
+                ++k;
+            }
+            double* y = work + (int64_t)k * n;
+            for (int64_t t = 0; t < n; ++t) y[t] = Xc[t * m + c];
+            householder_inplace(work, n, k + 1, k);
+            int singular = 0;
+            for (int32_t r = k - 1; r >= 0; --r) {
+                double s = y[r];
+                for (int32_t j = r + 1; j < k; ++j) s -= work[(int64_t)j * n + r] * bk[j];
+                const double rii = work[(int64_t)r * n + r];
+                if (!(fabs(rii) > 1e-12 * norm[r])) singular = 1;
+                bk[r] = s / rii;
+            }
+            double rss = 0.0;
+            for (int64_t t = k; t < n; ++t) rss += y[t] * y[t];
+            double icpt = mu[c];
+            for (int32_t j = 0; j < k; ++j) {
+                const double bj = singular ? NAN : bk[j];
+                b[cols[j]] = bj;
+                icpt -= bj * mu[cols[j]];
+            }
+            b[m] = icpt;
+            if (rss_out) rss_out[i] = rss;
+        }
+        free(work);
+    }
+    free(Xc);
+    return 0;
+}
+
 /* Direct oracle: every family solved on the centred data. */
 int oracle_scores(const double* X, int64_t n, int32_t m, double* rss_out, double* score_out,
                   int nthreads) {
@@ -232,6 +321,37 @@ int oracle_scores_sampled(const double* X, int64_t n, int32_t m, const int32_t* 
         }
         free(work);
     }
+    free(Xc);
+    return 0;
+}
+
+/* A list of families solved on the oracle's own m x m Householder factor R0
+ * of Xc (the R0-reduced variant: identical in exact arithmetic, m rows per
+ * family instead of n). */
+int oracle_scores_sampled_reduced(const double* X, int64_t n, int32_t m, const int32_t* child,
+                                  const uint64_t* mask, int64_t count, double* rss_out,
+                                  double* score_out, int nthreads) {
+    if (m < 1 || m > 30 || n < 1) return -1;
+    double* Xc = (double*)malloc(sizeof(double) * (size_t)n * (size_t)m);
+    double* R0 = (double*)malloc(sizeof(double) * (size_t)m * (size_t)m);
+    oracle_center(X, n, m, Xc);
+    oracle_r_factor(Xc, n, m, R0);
+#ifdef _OPENMP
+#pragma omp parallel num_threads(oracle_num_threads(nthreads))
+#endif
+    {
+        double* work = (double*)malloc(sizeof(double) * (size_t)m * (size_t)(m + 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1024)
+#endif
+        for (int64_t i = 0; i < count; ++i) {
+            double rss = oracle_family_rss(R0, m, m, child[i], mask[i], work);
+            if (rss_out) rss_out[i] = rss;
+            if (score_out) score_out[i] = oracle_bic(rss, n, popcount64(mask[i]));
+        }
+        free(work);
+    }
+    free(R0);
     free(Xc);
     return 0;
 }

@@ -13,10 +13,9 @@ static int max_q(int precision) { return precision ? kMaxQFp64 : kMaxQ; }
 
 int auto_q(int m, int precision) {
     // Small sub-walks keep the walk's unrolled code small (its instruction
-    // fetch is what bounds it), large ones need fewer roots; the tape of one
-    // sub-walk (2^Q - Q - 1 steps) stays in shared memory.  At m = 26 on a
-    // GB300 the whole call took 2.65 / 2.59 / 2.66 ms for Q = 6 / 7 / 8.
-    (void)precision;
+    // fetch bounds it), large ones need fewer roots; the tape of one sub-walk
+    // (2^Q - Q - 1 steps) stays in shared memory.  This rule is the fallback;
+    // givensbn_autotune measures the candidates on the device.
     int q = m - 19;
     if (q < 6) q = 6;
     if (q > 8) q = 8;
@@ -25,13 +24,70 @@ int auto_q(int m, int precision) {
     return q;
 }
 
+void shard_range(int64_t n_cta_total, int index, int count, int64_t* begin, int64_t* end) {
+    if (count <= 1) {
+        *begin = 0;
+        *end = n_cta_total;
+        return;
+    }
+    if (n_cta_total % 2 != 0) {  // a single CTA: shard 0 takes it
+        *begin = index == 0 ? 0 : n_cta_total;
+        *end = n_cta_total;
+        return;
+    }
+    const int64_t pairs = n_cta_total / 2;
+    *begin = 2 * (pairs * index / count);
+    *end = 2 * (pairs * (index + 1) / count);
+}
+
+// Consumer warps of the walk when the caller and the tuner leave it open:
+// enough that the largest CTA gives each a few columns to replay.
+static int auto_consumer_warps(const Plan& p) {
+    const int g = p.W >= 1 ? (p.lanes >> 1) : 1;
+    const int n5 = p.W >= 1 ? (p.W + (32 / g) - 1) / (32 / g) : 0;
+    const int items = p.Q + (p.k - p.W) + n5;
+    int nw = (items + kItemsPerWarp - 1) / kItemsPerWarp;
+    if (nw > 8) nw = 8;
+    return nw < 1 ? 1 : nw;
+}
+
 int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     if (m < GBN_MIN_M || m > GBN_MAX_M) return GBN_ERR_M;
     if (n < (int64_t)m + 1) return GBN_ERR_N;
     const int precision = opts ? opts->precision : 0;
     if (precision != 0 && precision != 1) return GBN_ERR_PRECISION;
-    int Q = (opts && opts->q > 0) ? opts->q : auto_q(m, precision);
+    const int cw_req = opts ? opts->consumer_warps : 0;
+    if (cw_req < 0 || cw_req > 8) return GBN_ERR_OPTS;
+    int Q = (opts && opts->q > 0) ? opts->q : 0;
+    int cw = cw_req;
+    if (Q == 0 && cw == 0 && opts && opts->tune_cache && !opts->debug_coverage) {
+        int tq = 0, tcw = 0;
+        if (tune_lookup(opts->tune_cache, 0, precision, m, m, 1, n, &tq, &tcw) && tq >= kMinQ &&
+            tq <= max_q(precision) && tq <= m && tcw >= 1 && tcw <= 8) {
+            Q = tq;
+            cw = tcw;
+        }
+    }
+    if (Q == 0) Q = auto_q(m, precision);
     if (Q < kMinQ || Q > max_q(precision) || Q > m) return GBN_ERR_Q;
+    const int score = opts ? opts->score : GBN_SCORE_BIC;
+    double lam;
+    switch (score) {
+        case GBN_SCORE_BIC: lam = log((double)n); break;
+        case GBN_SCORE_AIC: lam = 2.0; break;
+        case GBN_SCORE_PENALTY:
+            lam = opts->penalty;
+            if (!(lam == lam) || lam > 1e300 || lam < -1e300) return GBN_ERR_OPTS;
+            break;
+        default: return GBN_ERR_OPTS;
+    }
+    const int shard_count = opts ? opts->shard_count : 0;
+    const int shard_index = opts ? opts->shard_index : 0;
+    if (shard_count < 0 || shard_index < 0 || (shard_count <= 1 ? shard_index != 0
+                                                                  : shard_index >= shard_count))
+        return GBN_ERR_OPTS;
+    const long long wd = opts ? (long long)opts->watchdog_ns : 0;
+    if (wd < 0) return GBN_ERR_OPTS;
     *p = Plan();
     p->m = m;
     p->n = n;
@@ -40,7 +96,15 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     p->k = m - Q;
     p->W = p->k < kLaneBits ? p->k : kLaneBits;
     p->lanes = 1 << p->W;
-    p->n_cta = (int64_t)1 << (p->k - p->W);
+    p->n_cta_total = (int64_t)1 << (p->k - p->W);
+    int64_t cb = 0, ce = 0;
+    shard_range(p->n_cta_total, shard_index, shard_count, &cb, &ce);
+    p->cta_begin = cb;
+    p->n_cta = ce - cb;
+    p->lam = lam;
+    const int mp = opts ? opts->max_parents : -1;
+    p->kmax = (mp < 0 || mp > m - 1) ? m - 1 : mp;
+    p->watchdog_ns = wd > 0 ? wd : kWatchdogNs;
     int pos = 0;
     for (int v = p->W; v < p->k; ++v) p->order[pos++] = v;
     for (int v = p->W - 1; v >= 0; --v) p->order[pos++] = v;
@@ -54,14 +118,7 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     p->coverage = opts ? (opts->debug_coverage != 0) : 0;
     const size_t es = precision ? sizeof(double) : sizeof(float);
     p->leaf_stride = leaf_stride_elems(Q, p->k);
-    {  // consumer warps: enough that the largest CTA gives each a few columns to replay
-        const int g = p->W >= 1 ? (p->lanes >> 1) : 1;
-        const int n5 = p->W >= 1 ? (p->W + (32 / g) - 1) / (32 / g) : 0;
-        const int items = Q + (p->k - p->W) + n5;
-        int nw = (items + kItemsPerWarp - 1) / kItemsPerWarp;
-        if (nw > 8) nw = 8;
-        p->n_bwarps = nw < 1 ? 1 : nw;
-    }
+    p->n_bwarps = cw > 0 ? cw : auto_consumer_warps(*p);
     size_t off = 0;
     p->off_status = off;
     off = align_up(off + 256, 256);
@@ -154,6 +211,32 @@ void givensbn_default_opts(givensbn_opts* opts) {
     memset(opts, 0, sizeof(*opts));
     opts->center = 1;
     opts->fixup_tau = 1e-6;
+    opts->max_parents = -1;
+    opts->score = GBN_SCORE_BIC;
+}
+
+int givensbn_plan_choice(int64_t n, int32_t m, const givensbn_opts* opts, int32_t* q,
+                         int32_t* consumer_warps) {
+    if (!q || !consumer_warps) return GBN_ERR_NULL;
+    Plan p;
+    const int rc = make_plan(n, m, opts, &p);
+    if (rc) return rc;
+    *q = p.Q;
+    *consumer_warps = p.n_bwarps;
+    return GBN_OK;
+}
+
+int givensbn_shard_range(int64_t n, int32_t m, const givensbn_opts* opts, int32_t* fixed_k,
+                         int32_t* lane_bits, int64_t* cta_begin, int64_t* cta_end) {
+    if (!fixed_k || !lane_bits || !cta_begin || !cta_end) return GBN_ERR_NULL;
+    Plan p;
+    const int rc = make_plan(n, m, opts, &p);
+    if (rc) return rc;
+    *fixed_k = p.k;
+    *lane_bits = p.W;
+    *cta_begin = p.cta_begin;
+    *cta_end = p.cta_begin + p.n_cta;
+    return GBN_OK;
 }
 
 int32_t givensbn_auto_q(int32_t m, int32_t precision) { return auto_q(m, precision); }
@@ -209,6 +292,10 @@ const char* givensbn_strerror(int code) {
         case GBN_ERR_STATIC_SCRATCH:
             return "input too large for the 16 MiB static scratch of score_all_families_noalloc "
                    "(m <= 20 with the automatic q)";
+        case GBN_ERR_OPTS:
+            return "an option is outside its range (score, penalty, shard, consumer warps, "
+                   "watchdog) or not supported by this entry point";
+        case GBN_ERR_TUNE: return "the autotuner could not time or record a candidate";
         default: return "unknown error";
     }
 }

@@ -279,9 +279,13 @@ int make_bwd_plan(int64_t n, int32_t m, const givensbn_opts* opts, BwdPlan* b) {
     givensbn_opts o;
     givensbn_default_opts(&o);
     if (opts) o = *opts;
+    if (o.shard_count > 1) return GBN_ERR_OPTS;  // the gradient sums over every family
     const int qreq = o.q;
     o.q = 0;
+    o.consumer_warps = 0;
+    o.tune_cache = nullptr;
     o.debug_coverage = 0;
+    o.fixup_tau = 0.0;  // no fix-up stage: its workspace region is reused below
     int rc = make_plan(n, m, &o, &b->p);
     if (rc) return rc;
     int Qb = qreq > 0 ? qreq : m - 10;
@@ -328,14 +332,19 @@ int launch_bwd(const BwdPlan& b, const double* X, const void* w, double* grad, c
                              (int)smem) != cudaSuccess)
         return GBN_ERR_CUDA;
     const unsigned blocks = (unsigned)((b.total_warps + kBwdWarps - 1) / kBwdWarps);
-    bwd_walk_kernel<T><<<blocks, 32 * kBwdWarps, smem, stream>>>(g);
     double* gsym = reinterpret_cast<double*>(ws + b.off_gsym);
     double* muv = reinterpret_cast<double*>(ws + b.off_muv);
-    bwd_reduce_kernel<<<8, 256, 0, stream>>>(g.partials, b.total_warps, p.m,
-                                             reinterpret_cast<const double*>(ws + p.off_mu), p,
-                                             gsym, muv);
-    bwd_grad_kernel<<<304, 256, 0, stream>>>(X, p.n, p.m, gsym, muv, grad);
-    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+    const double* mu = reinterpret_cast<const double*>(ws + p.off_mu);
+    const double* partials = g.partials;
+    const cudaError_t e[] = {
+        launch_plain(bwd_walk_kernel<T>, dim3(blocks), dim3(32 * kBwdWarps), smem, stream, g),
+        launch_plain(bwd_reduce_kernel, dim3(8), dim3(256), 0, stream, partials, b.total_warps, p.m,
+                     mu, p, gsym, muv),
+        launch_plain(bwd_grad_kernel, dim3(304), dim3(256), 0, stream, X, p.n, p.m,
+                     (const double*)gsym, (const double*)muv, grad)};
+    for (cudaError_t x : e)
+        if (x != cudaSuccess) return GBN_ERR_CUDA;
+    return GBN_OK;
 }
 
 }  // namespace

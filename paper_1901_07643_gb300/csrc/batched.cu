@@ -56,14 +56,30 @@ int plan_batch(const int64_t* ns, const int32_t* ms, int32_t B, const givensbn_o
     if (opts) o = *opts;
     int precision = o.precision;
     if (precision != 0 && precision != 1) return GBN_ERR_PRECISION;
-    // one Q for the whole batch: the requested one, else the smallest automatic choice
+    if (o.shard_count > 1) return GBN_ERR_OPTS;  // sharding splits one table, not a batch
+    int mmin = GBN_MAX_M, mmax = GBN_MIN_M;
+    int64_t nsum = 0;
+    for (int b = 0; b < B; ++b) {
+        if (ms[b] < GBN_MIN_M || ms[b] > GBN_MAX_M) return GBN_ERR_M;
+        mmin = std::min(mmin, (int)ms[b]);
+        mmax = std::max(mmax, (int)ms[b]);
+        nsum += ns[b];
+    }
+    // one Q for the whole batch: the requested one, else the autotuner's cached
+    // choice for this batch's size class, else the smallest automatic choice
     int Q = o.q;
+    if (Q <= 0 && o.consumer_warps == 0 && o.tune_cache && !o.debug_coverage) {
+        int tq = 0, tcw = 0;
+        if (tune_lookup(o.tune_cache, 1, precision, mmax, mmin, B, nsum, &tq, &tcw) &&
+            tq >= kMinQ && tq <= mmin && tq <= (precision ? kMaxQFp64 : kMaxQ) && tcw >= 1 &&
+            tcw <= 8) {
+            Q = tq;
+            o.consumer_warps = tcw;
+        }
+    }
     if (Q <= 0) {
         Q = 1 << 30;
-        for (int b = 0; b < B; ++b) {
-            if (ms[b] < GBN_MIN_M || ms[b] > GBN_MAX_M) return GBN_ERR_M;
-            Q = std::min(Q, auto_q(ms[b], precision));
-        }
+        for (int b = 0; b < B; ++b) Q = std::min(Q, auto_q(ms[b], precision));
     }
     o.q = Q;
     o.fixup_tau = 0.0;  // the FP64 fix-up pass belongs to the single-dataset entry point
@@ -132,8 +148,8 @@ int upload(const std::vector<unsigned char>& host, char* dst, cudaStream_t strea
         chunk.dst = reinterpret_cast<unsigned char*>(dst + pos);
         chunk.bytes = (int)nb;
         memcpy(chunk.data, host.data() + pos, nb);
-        upload_kernel<<<32, 256, 0, stream>>>(chunk);
-        if (cudaGetLastError() != cudaSuccess) return GBN_ERR_CUDA;
+        if (launch_plain(upload_kernel, dim3(32), dim3(256), 0, stream, chunk) != cudaSuccess)
+            return GBN_ERR_CUDA;
     }
     return GBN_OK;
 }
@@ -224,7 +240,7 @@ extern "C" int score_all_families_batched(const double* const* Xs, const int64_t
     v.pairs = (precision == 0 && opts->debug_coverage == 0) ? 1 : 0;
     for (int b = 0; b < B && v.pairs; ++b) {  // the paired walk's conditions, for every dataset
         const Plan& pb = L.plans[b];
-        if (pb.W != 5 || pb.lanes != 32 || pb.n_cta % 2 != 0) v.pairs = 0;
+        if (pb.W != 5 || pb.lanes != 32 || pb.n_cta % 2 != 0 || pb.kmax < pb.m - 1) v.pairs = 0;
     }
     int max_m = 1;
     for (int b = 0; b < B; ++b) max_m = std::max(max_m, L.plans[b].m);

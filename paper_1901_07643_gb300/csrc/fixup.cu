@@ -62,6 +62,18 @@ __global__ void __launch_bounds__(1024) fix_flags_kernel(const Plan p, char* ws)
 
 constexpr int kScanBlocksPerChild = 64;
 
+// Whether this call wrote slot s (compressed parent mask) of child c: the
+// family's parent count is within the bound, and with sharding its sub-walk
+// CTA, (S & H) >> W with H the fixed variables 0..k-1, is in the call's range.
+__device__ __forceinline__ bool slot_written(const Plan& p, int c, int64_t s) {
+    const uint64_t cs = (uint64_t)s;
+    if (__popcll(cs) > p.kmax) return false;
+    if (!p.sharded()) return true;
+    const uint64_t S = (cs & ((1ull << c) - 1ull)) | ((cs >> c) << (c + 1));
+    const int64_t g = (int64_t)((S & ((1ull << p.k) - 1ull)) >> p.W);
+    return g >= p.cta_begin && g < p.cta_begin + p.n_cta;
+}
+
 // List the families of flagged children whose score is below the threshold.
 __global__ void fix_scan_kernel(const Plan p, char* ws, const float* __restrict__ out) {
     grid_dep_wait();
@@ -70,7 +82,7 @@ __global__ void fix_scan_kernel(const Plan p, char* ws, const float* __restrict_
     const unsigned mask = *reinterpret_cast<const unsigned*>(ws + p.off_fix);
     if (!((mask >> c) & 1u)) return;
     const float base = reinterpret_cast<const float*>(ws + p.off_fix + 16)[c];  // n ln(thr/n)
-    const float lnn = (float)log((double)p.n);
+    const float lam = (float)p.lam;
     unsigned* count = reinterpret_cast<unsigned*>(ws + p.off_status + kFixCountOffset);
     long long* list = reinterpret_cast<long long*>(ws + p.off_fix + 256);
     int* status = reinterpret_cast<int*>(ws + p.off_status);
@@ -84,9 +96,9 @@ __global__ void fix_scan_kernel(const Plan p, char* ws, const float* __restrict_
          s0 += stride) {
         const int64_t s = s0 + lane;
         bool f = false;
-        if (s < block) {
+        if (s < block && slot_written(p, c, s)) {
             const float sc = out[((int64_t)c << (m - 1)) + s];
-            f = sc < base + (float)__popcll((unsigned long long)s) * lnn;
+            f = sc < base + (float)__popcll((unsigned long long)s) * lam;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, f);
         if (bal) {
@@ -122,7 +134,7 @@ __global__ void __launch_bounds__(32 * kFixWarps) fixup_kernel(const Plan p, cha
     const long long* list = reinterpret_cast<const long long*>(ws + p.off_fix + 256);
     const double* R0 = reinterpret_cast<const double*>(ws + p.off_r0);
     double* Mw = M + warp * 32 * kLdF;
-    const double n = (double)p.n, lnn = log(n);
+    const double n = (double)p.n, lam = p.lam;
     const long long table = (long long)m << (m - 1);
     for (unsigned i = blockIdx.x * kFixWarps + warp; i < count; i += gridDim.x * kFixWarps) {
         const long long slot = list[i];
@@ -156,7 +168,7 @@ __global__ void __launch_bounds__(32 * kFixWarps) fixup_kernel(const Plan p, cha
         }
         const double t = (lane >= k && lane < m) ? Mw[lane * kLdF + k] : 0.0;
         const double rss = warp_sum(t * t);
-        if (lane == 0) out[slot] = rss > 0.0 ? (float)(n * log(rss / n) + k * lnn) : -INFINITY;
+        if (lane == 0) out[slot] = rss > 0.0 ? (float)(n * log(rss / n) + k * lam) : -INFINITY;
         __syncwarp();
     }
 }
@@ -164,9 +176,7 @@ __global__ void __launch_bounds__(32 * kFixWarps) fixup_kernel(const Plan p, cha
 }  // namespace
 
 int launch_fix_flags(const Plan& p, char* ws, cudaStream_t stream) {
-    if (launch_dep(fix_flags_kernel, dim3(1), dim3(1024), 0, stream, p, ws) != cudaSuccess)
-        return GBN_ERR_CUDA;
-    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+    return launch_rc(launch_dep(fix_flags_kernel, dim3(1), dim3(1024), 0, stream, p, ws));
 }
 
 int launch_fixup(const Plan& p, char* ws, void* out, cudaStream_t stream) {
@@ -175,7 +185,7 @@ int launch_fixup(const Plan& p, char* ws, void* out, cudaStream_t stream) {
         launch_dep(fixup_kernel, dim3(304), dim3(32 * kFixWarps), 0, stream, p, ws,
                    static_cast<float*>(out)) != cudaSuccess)
         return GBN_ERR_CUDA;
-    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+    return GBN_OK;
 }
 
 }  // namespace gbn

@@ -52,7 +52,9 @@ struct Plan {
     int k = 0;        // fixed variables = m - Q (the bits of Algorithm 2's processor code)
     int W = 0;        // fixed variables that vary across the lanes of a warp, min(5, k)
     int lanes = 0;    // 2^W sub-walks per CTA
-    int64_t n_cta = 0;  // 2^(k-W) CTAs
+    int64_t n_cta = 0;        // sub-walk CTAs of this call (all 2^(k-W) unless sharded)
+    int64_t n_cta_total = 0;  // 2^(k-W): sub-walk CTAs of the whole table
+    int64_t cta_begin = 0;    // global index of this call's first CTA (even when n_cta is)
     int order[32] = {}; // column order of R0: [W..k-1, W-1..0, k..m-1]
     int panels = 0;
     int rows_per_panel = 0;
@@ -70,7 +72,22 @@ struct Plan {
     size_t total_bytes = 0;
     size_t leaf_stride = 0;  // elements per CTA leaf record
     int n_bwarps = 1;        // consumer warps per walk CTA (they loop over the CTA's columns)
+    double lam = 0.0;        // score penalty per parent (ln n: BIC, 2: AIC, or the caller's)
+    int kmax = 0;            // in-degree bound: families with more parents are not written (m-1: none)
+    long long watchdog_ns = 0;  // bound on every wait between the warps of a walk block
+    __host__ __device__ bool sharded() const { return cta_begin != 0 || n_cta != n_cta_total; }
 };
+
+// A wait inside the walk that lasts this long means the schedule is broken.
+constexpr long long kWatchdogNs = 2000000000ll;
+
+// Sub-walk CTAs [*begin, *end) of shard `index` of `count` (the table split
+// into contiguous ranges of CTA pairs, so that every range starts even).
+void shard_range(int64_t n_cta_total, int index, int count, int64_t* begin, int64_t* end);
+// The autotuner's cached (q, consumer warps) for this device and size class;
+// false when the cache has no usable entry.
+bool tune_lookup(const char* path, int batched, int precision, int m, int mmin, int64_t count,
+                 int64_t n, int* q, int* cw);
 
 int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* plan);
 int auto_q(int m, int precision);
@@ -153,6 +170,23 @@ inline cudaError_t launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
+
+// A plain launch whose own error is returned (cudaLaunchKernelEx reports the
+// launch's error without reading or clearing the thread's sticky error state,
+// which may hold an error of the caller's unrelated work).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_plain(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                cudaStream_t stream, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = nullptr;
+    cfg.numAttrs = 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+inline int launch_rc(cudaError_t e) { return e == cudaSuccess ? GBN_OK : GBN_ERR_CUDA; }
 
 __device__ __forceinline__ int batch_locate(const BatchView& v, const int64_t* prefix, int64_t bx,
                                             int64_t& local) {

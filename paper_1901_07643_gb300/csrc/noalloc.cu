@@ -21,7 +21,10 @@
 //    so a call must not start (on any stream or host thread) until the
 //    previous call's kernels have finished.
 //  * The first call on a device does the symbol lookup; make that first call
-//    before any stream capture begins.
+//    before any stream capture begins.  The address is kept for the life of
+//    the process: after cudaDeviceReset (or anything else that destroys the
+//    device's primary context) it names memory of the old context, so a
+//    process that resets a device must not call this entry point again.
 #include <mutex>
 
 #include "gbn_internal.cuh"

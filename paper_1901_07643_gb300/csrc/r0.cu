@@ -394,7 +394,9 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel_b(const BatchView v,
 
 int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream) {
     if (cudaMemsetAsync(ws + p.off_status, 0, 256, stream) != cudaSuccess) return GBN_ERR_CUDA;
-    if (p.center) colsum_kernel<<<p.panels, 256, 0, stream>>>(p, X, ws);
+    if (p.center &&
+        launch_plain(colsum_kernel, dim3(p.panels), dim3(256), 0, stream, p, X, ws) != cudaSuccess)
+        return GBN_ERR_CUDA;
     const unsigned groups = (unsigned)((p.m * (p.m + 1) / 2 + 31) / 32);
     const cudaError_t e[] = {
         launch_dep(mean_kernel, dim3(1), dim3(kRedThreads), 0, stream, p, ws),
@@ -406,22 +408,25 @@ int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream) {
         launch_dep(chol_kernel, dim3(1), dim3(kCholThreads), 0, stream, p, ws, 1)};
     for (cudaError_t x : e)
         if (x != cudaSuccess) return GBN_ERR_CUDA;
-    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+    return GBN_OK;
 }
 
 int launch_r0_batched(const BatchView& v, int64_t total_panels, int max_m, cudaStream_t stream) {
     const unsigned B = (unsigned)v.B, P = (unsigned)total_panels;
-    status_clear_kernel_b<<<B, 64, 0, stream>>>(v);
-    colsum_kernel_b<<<P, 256, 0, stream>>>(v);
-    mean_kernel_b<<<B, kRedThreads, 0, stream>>>(v);
     const dim3 sum_grid((unsigned)((max_m * (max_m + 1) / 2 + 31) / 32), B);
-    gram_kernel_b<<<P, 512, 0, stream>>>(v, 0);
-    gram_sum_kernel_b<<<sum_grid, kRedThreads, 0, stream>>>(v);
-    chol_kernel_b<<<B, kCholThreads, 0, stream>>>(v, 0);
-    gram_kernel_b<<<P, 512, 0, stream>>>(v, 1);
-    gram_sum_kernel_b<<<sum_grid, kRedThreads, 0, stream>>>(v);
-    chol_kernel_b<<<B, kCholThreads, 0, stream>>>(v, 1);
-    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+    const cudaError_t e[] = {
+        launch_plain(status_clear_kernel_b, dim3(B), dim3(64), 0, stream, v),
+        launch_plain(colsum_kernel_b, dim3(P), dim3(256), 0, stream, v),
+        launch_plain(mean_kernel_b, dim3(B), dim3(kRedThreads), 0, stream, v),
+        launch_plain(gram_kernel_b, dim3(P), dim3(512), 0, stream, v, 0),
+        launch_plain(gram_sum_kernel_b, sum_grid, dim3(kRedThreads), 0, stream, v),
+        launch_plain(chol_kernel_b, dim3(B), dim3(kCholThreads), 0, stream, v, 0),
+        launch_plain(gram_kernel_b, dim3(P), dim3(512), 0, stream, v, 1),
+        launch_plain(gram_sum_kernel_b, sum_grid, dim3(kRedThreads), 0, stream, v),
+        launch_plain(chol_kernel_b, dim3(B), dim3(kCholThreads), 0, stream, v, 1)};
+    for (cudaError_t x : e)
+        if (x != cudaSuccess) return GBN_ERR_CUDA;
+    return GBN_OK;
 }
 
 }  // namespace gbn

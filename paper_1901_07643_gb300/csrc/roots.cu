@@ -147,15 +147,17 @@ __device__ __forceinline__ void top_store(const T* S, const TopNode<T>& nd, T* _
     if (lane == 0) *mask_of(out, nd.rows) = nd.carried;
 }
 
-// One walk CTA's root: its path through the k - W top levels.
+// One walk CTA's root: its path through the k - W top levels (the bits of
+// its global index g), stored at slot `local` of this call's nodes.
 template <typename T>
 __device__ __forceinline__ void top_body(const double* __restrict__ R0, const Plan& p,
                                          T* __restrict__ top, unsigned long long* chk,
-                                         uint64_t cta, T* S /* 32 x 32, [row * 32 + lane] */) {
+                                         uint64_t g, uint64_t local,
+                                         T* S /* 32 x 32, [row * 32 + lane] */) {
     TopNode<T> nd;
     top_load(R0, p, chk, S, nd);
-    for (int f = 0; f < p.k - p.W; ++f) top_decide(S, nd, f, ((cta >> f) & 1ull) != 0);
-    top_store(S, nd, top, cta);
+    for (int f = 0; f < p.k - p.W; ++f) top_decide(S, nd, f, ((g >> f) & 1ull) != 0);
+    top_store(S, nd, top, local);
 }
 
 // The roots of 2^d walk CTAs at once: they share the path through the first
@@ -695,6 +697,8 @@ __global__ void __launch_bounds__(32 * kDfsWarps, (std::is_same<T, float>::value
     const uint64_t gw = (uint64_t)blockIdx.x * kDfsWarps + warp;
     const uint64_t cta = gw / kWarpsPerCta;
     if (cta >= (uint64_t)p.n_cta) return;
+    // a walk CTA whose front sets all exceed the in-degree bound is not walked
+    if (__popcll(cta + (uint64_t)p.cta_begin) > p.kmax) return;
     T* stack = reinterpret_cast<T*>(smem_raw) + warp * leaf_warp_elems<T>(p);
     T* leaves = reinterpret_cast<T*>(ws + p.off_leaves);
     unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
@@ -718,7 +722,21 @@ __global__ void __launch_bounds__(32 * kTopWarps) roots_top_kernel_b(const Batch
     char* ws = v.ws[d];
     top_body<T>(reinterpret_cast<const double*>(ws + p.off_r0), p, top_nodes<T>(p, ws),
                 reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset),
-                (uint64_t)local, S + warp * 32 * 32);
+                (uint64_t)local, (uint64_t)local, S + warp * 32 * 32);
+}
+
+// One dataset, a shard of the table: one warp per walk CTA of the shard, each
+// following its own path (global index cta_begin + local).
+template <typename T>
+__global__ void __launch_bounds__(32 * kTopWarps) roots_top_kernel(const Plan p, char* ws) {
+    __shared__ T S[kTopWarps * 32 * 32];
+    grid_dep_wait();
+    const int warp = threadIdx.x >> 5;
+    const int64_t local = (int64_t)blockIdx.x * kTopWarps + warp;
+    if (local >= p.n_cta) return;
+    top_body<T>(reinterpret_cast<const double*>(ws + p.off_r0), p, top_nodes<T>(p, ws),
+                reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset),
+                (uint64_t)(p.cta_begin + local), (uint64_t)local, S + warp * 32 * 32);
 }
 
 template <typename T>
@@ -758,15 +776,24 @@ int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
     if (p.Q + p.W > kDfsRows) return GBN_ERR_Q;
     const size_t smem = sizeof(T) * leaf_warp_elems<T>(p) * kDfsWarps;
     if (smem > 227 * 1024) return GBN_ERR_Q;
-    const uint64_t groups = (uint64_t)p.n_cta >> top_dfs_levels(p);
-    const unsigned nb_top = (unsigned)((groups + kTopDfsWarps - 1) / kTopDfsWarps);
-    const size_t smem_top = sizeof(T) * (32 * 32 + top_dfs_stack_elems(p)) * kTopDfsWarps;
-    if (cudaFuncSetAttribute(roots_top_dfs_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_top) != cudaSuccess)
-        return GBN_ERR_CUDA;
-    if (launch_dep(roots_top_dfs_kernel<T>, dim3(nb_top), dim3(32 * kTopDfsWarps), smem_top, stream,
-                   p, ws) != cudaSuccess)
-        return GBN_ERR_CUDA;
+    if (p.n_cta < 1) return GBN_OK;  // an empty shard
+    if (p.sharded()) {  // one path per CTA of the shard
+        const unsigned nb = (unsigned)((p.n_cta + kTopWarps - 1) / kTopWarps);
+        if (launch_dep(roots_top_kernel<T>, dim3(nb), dim3(32 * kTopWarps), 0, stream, p, ws) !=
+            cudaSuccess)
+            return GBN_ERR_CUDA;
+    } else {  // subtrees of 2^d CTAs enumerated depth first
+        const uint64_t groups = (uint64_t)p.n_cta >> top_dfs_levels(p);
+        const unsigned nb_top = (unsigned)((groups + kTopDfsWarps - 1) / kTopDfsWarps);
+        const size_t smem_top = sizeof(T) * (32 * 32 + top_dfs_stack_elems(p)) * kTopDfsWarps;
+        if (cudaFuncSetAttribute(roots_top_dfs_kernel<T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_top) != cudaSuccess)
+            return GBN_ERR_CUDA;
+        if (launch_dep(roots_top_dfs_kernel<T>, dim3(nb_top), dim3(32 * kTopDfsWarps), smem_top,
+                       stream, p, ws) != cudaSuccess)
+            return GBN_ERR_CUDA;
+    }
     int rc;
     switch (p.W == 5 ? p.Q : 0) {
         case 4: rc = launch_leaves_q<T, 4>(p, ws, smem, stream); break;
@@ -777,8 +804,7 @@ int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
         case 9: rc = launch_leaves_q<T, 9>(p, ws, smem, stream); break;
         default: rc = launch_leaves_q<T, 0>(p, ws, smem, stream); break;
     }
-    if (rc) return rc;
-    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+    return rc;
 }
 
 // A batch whose datasets all have W = 5 (FP32, a compiled Q): the two-warp
@@ -810,8 +836,8 @@ int launch_leaves_bq(const BatchView& v, int64_t total_cta, size_t max_stride,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return GBN_ERR_CUDA;
     const unsigned nb = (unsigned)((2 * total_cta + kDfsWarps - 1) / kDfsWarps);
-    roots_leaves_kernel_bq<T, QF><<<nb, 32 * kDfsWarps, smem, stream>>>(v, max_stride);
-    return GBN_OK;
+    return launch_rc(launch_plain(roots_leaves_kernel_bq<T, QF>, dim3(nb), dim3(32 * kDfsWarps),
+                                  smem, stream, v, max_stride));
 }
 
 template <typename T>
@@ -825,7 +851,9 @@ int launch_roots_batched_t(const BatchView& v, int64_t total_cta, int Q, int max
         return GBN_ERR_CUDA;
     const unsigned nb_top = (unsigned)((total_cta + kTopWarps - 1) / kTopWarps);
     const unsigned nb_dfs = (unsigned)((total_cta + kDfsWarps - 1) / kDfsWarps);
-    roots_top_kernel_b<T><<<nb_top, 32 * kTopWarps, 0, stream>>>(v);
+    if (launch_plain(roots_top_kernel_b<T>, dim3(nb_top), dim3(32 * kTopWarps), 0, stream, v) !=
+        cudaSuccess)
+        return GBN_ERR_CUDA;
     bool reg = false;
     if constexpr (std::is_same<T, float>::value) reg = v.pairs && leaves_in_registers<T>(Q, 5);
     if (reg) {
@@ -840,11 +868,10 @@ int launch_roots_batched_t(const BatchView& v, int64_t total_cta, int Q, int max
                 default: rc = launch_leaves_bq<T, 9>(v, total_cta, max_stride, stream); break;
             }
         }
-        if (rc) return rc;
-    } else {
-        roots_leaves_kernel_b<T><<<nb_dfs, 32 * kDfsWarps, smem, stream>>>(v, Q, max_w, max_stride);
+        return rc;
     }
-    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+    return launch_rc(launch_plain(roots_leaves_kernel_b<T>, dim3(nb_dfs), dim3(32 * kDfsWarps), smem,
+                                  stream, v, Q, max_w, max_stride));
 }
 
 }  // namespace

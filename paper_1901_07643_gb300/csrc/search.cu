@@ -1,0 +1,262 @@
+// Exact structure search over the local-score table: the use of the
+// all-family scores that motivates the method (Sec. 1: structure learning of
+// a Bayesian network from every child / parent-set score).
+//
+// With scores where lower is better and no constraint but acyclicity, an
+// optimal DAG is found by dynamic programming over variable subsets:
+//   1. best parents: B[c][U] = min over S subset of U of score(c, S), for every
+//      child c and candidate set U of the other variables, with its argmin;
+//   2. sinks: F[W] = min over c in W of F[W \ c] + B[c][W \ c], F[empty] = 0,
+//      the score of the best network on the variables W (c is W's sink, the
+//      last variable of an optimal ordering of W);
+//   3. backtracking from W = V through the recorded sinks gives an optimal
+//      ordering and, with the argmins of step 1, the parent set of each
+//      variable.
+// Step 1 is a subset-minimum transform of each child's 2^(m-1) block (one bit
+// of the compressed parent mask at a time; a block of bits per pass through a
+// shared-memory tile, so HBM is read and written once per pass, 3 passes at
+// m = 26); step 2 runs one launch per subset size, threads over the subsets of
+// that size (unranked in the combinatorial number system), in FP64.
+// Ties: the smaller candidate set (the subset) in step 1, the smallest sink in
+// step 2, so the result is deterministic.
+#include <math.h>
+
+#include "gbn_internal.cuh"
+
+namespace gbn {
+namespace {
+
+constexpr int kFirstBits = 12;  // bits of the first (contiguous) pass: 4096-entry tiles
+constexpr int kPassBits = 9;    // bits of each later pass: 512 rows x 8 columns
+constexpr int kCols = 8;        // consecutive entries per row of a strided tile (32 bytes)
+constexpr int kTileThreads = 512;
+
+// One tile in shared memory: R rows (stride `rs` apart in the child block)
+// of C consecutive entries; the transform runs over the row bits.
+__device__ __forceinline__ void tile_transform(float* v, uint32_t* s, int rbits, int C) {
+    const int rows = 1 << rbits;
+    for (int b = 0; b < rbits; ++b) {
+        const int half = rows >> 1;
+        for (int e = threadIdx.x; e < half * C; e += blockDim.x) {
+            const int pr = e / C, col = e % C;
+            // pair (lo, hi) of rows differing in bit b: lo has it clear
+            const int lo = ((pr >> b) << (b + 1)) | (pr & ((1 << b) - 1));
+            const int hi = lo | (1 << b);
+            const float a = v[lo * C + col], x = v[hi * C + col];
+            if (a <= x) {  // the subset wins ties
+                v[hi * C + col] = a;
+                s[hi * C + col] = s[lo * C + col];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Pass over bits [b0, b0 + rbits) of every child block.  Tile t of a block:
+// its column group (bits below b0, kCols entries at a time) and its high bits.
+// First pass (b0 = 0): rows of one entry, and the sets start as the slots'
+// own compressed masks.
+__global__ void __launch_bounds__(kTileThreads)
+    bps_pass_kernel(const float* __restrict__ src, float* __restrict__ best,
+                    uint32_t* __restrict__ bset, int m, int b0, int rbits, int first) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int C = first ? 1 : kCols;
+    const int rows = 1 << rbits;
+    float* v = reinterpret_cast<float*>(smem);
+    uint32_t* s = reinterpret_cast<uint32_t*>(smem + sizeof(float) * rows * C);
+    const int64_t block = (int64_t)1 << (m - 1);
+    const int64_t groups_lo = first ? 1 : ((int64_t)1 << b0) / kCols;  // column groups
+    const int64_t tiles_per_child = block / ((int64_t)rows * C);
+    const int64_t t = blockIdx.x;
+    const int64_t child = t / tiles_per_child;
+    const int64_t r = t % tiles_per_child;
+    const int64_t lo = r % groups_lo, hi = r / groups_lo;
+    const int64_t base = child * block + (hi << (b0 + rbits)) + lo * C;
+    for (int e = threadIdx.x; e < rows * C; e += blockDim.x) {
+        const int row = e / C, col = e % C;
+        const int64_t idx = base + ((int64_t)row << b0) + col;
+        v[e] = (first ? src : best)[idx];
+        s[e] = first ? (uint32_t)(idx - child * block) : bset[idx];
+    }
+    __syncthreads();
+    tile_transform(v, s, rbits, C);
+    for (int e = threadIdx.x; e < rows * C; e += blockDim.x) {
+        const int row = e / C, col = e % C;
+        const int64_t idx = base + ((int64_t)row << b0) + col;
+        best[idx] = v[e];
+        bset[idx] = s[e];
+    }
+}
+
+// The rank-th p-subset of {0..m-1} (combinatorial number system, largest
+// element first) as a bitmask; binom[x * 33 + k] = C(x, k).
+__device__ __forceinline__ uint32_t unrank(long long rank, int p, int m, const long long* binom) {
+    uint32_t w = 0;
+    int x = m - 1;
+    for (int k = p; k >= 1; --k) {
+        while (binom[x * 33 + k] > rank) --x;  // the largest x with C(x, k) <= rank
+        rank -= binom[x * 33 + k];
+        w |= 1u << x;
+        --x;
+    }
+    return w;
+}
+
+__device__ __forceinline__ uint32_t compress_mask(uint32_t U, int c) {
+    return (U & ((1u << c) - 1u)) | ((U >> (c + 1)) << c);
+}
+
+// Subsets W of size p: F[W] and its sink.
+__global__ void dp_layer_kernel(const float* __restrict__ best, double* __restrict__ F,
+                                uint8_t* __restrict__ sink, int m, int p, long long count) {
+    __shared__ long long binom[32 * 33];
+    for (int e = threadIdx.x; e < m * 33; e += blockDim.x) {  // C(x, k), x < m, k <= 32
+        const int x = e / 33, k = e % 33;
+        long long c = k <= x ? 1 : 0;
+        for (int i = 1; i <= k && i <= x; ++i) c = c * (x - k + i) / i;  // exact at every step
+        binom[e] = c;
+    }
+    __syncthreads();
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= count) return;
+    const uint32_t W = unrank(r, p, m, binom);
+    const int64_t block = (int64_t)1 << (m - 1);
+    double fbest = INFINITY;
+    int cbest = 0;
+    for (uint32_t rest = W; rest; rest &= rest - 1) {
+        const int c = __ffs(rest) - 1;
+        const uint32_t U = W & ~(1u << c);
+        const double val = F[U] + (double)best[(int64_t)c * block + compress_mask(U, c)];
+        if (val < fbest) {  // strict: the smallest sink wins ties
+            fbest = val;
+            cbest = c;
+        }
+    }
+    F[W] = fbest;
+    sink[W] = (uint8_t)cbest;
+}
+
+__global__ void dp_init_kernel(double* F) { F[0] = 0.0; }
+
+// Backtracking from the full set: one thread, m steps.
+__global__ void backtrack_kernel(const double* __restrict__ F, const uint8_t* __restrict__ sink,
+                                 const uint32_t* __restrict__ bset, int m,
+                                 uint32_t* __restrict__ parents, int32_t* __restrict__ order,
+                                 double* __restrict__ total) {
+    const int64_t block = (int64_t)1 << (m - 1);
+    uint32_t W = (m == 32) ? 0xffffffffu : ((1u << m) - 1u);
+    total[0] = F[W];
+    for (int step = m - 1; step >= 0; --step) {
+        const int c = sink[W];
+        const uint32_t U = W & ~(1u << c);
+        const uint32_t cs = bset[(int64_t)c * block + compress_mask(U, c)];
+        parents[c] = (cs & ((1u << c) - 1u)) | ((cs >> c) << (c + 1));  // expand: re-insert bit c
+        if (order) order[step] = c;
+        W = U;
+    }
+}
+
+struct SearchLayout {
+    size_t off_best = 0, off_set = 0, off_F = 0, off_sink = 0, total = 0;
+};
+
+SearchLayout search_layout(int m) {
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t table = (size_t)m << (m - 1);
+    SearchLayout L;
+    size_t off = 0;
+    L.off_best = off;
+    off = up(off + sizeof(float) * table);
+    L.off_set = off;
+    off = up(off + sizeof(uint32_t) * table);
+    L.off_F = off;
+    off = up(off + sizeof(double) * ((size_t)1 << m));
+    L.off_sink = off;
+    off = up(off + ((size_t)1 << m));
+    L.total = off;
+    return L;
+}
+
+int run_bps(const float* scores, int m, float* best, uint32_t* bset, cudaStream_t stream) {
+    const int bits = m - 1;
+    const int64_t table = (int64_t)m << (m - 1);
+    int b0 = 0;
+    bool first = true;
+    while (first || b0 < bits) {
+        int rb, C;
+        if (first) {
+            rb = bits < kFirstBits ? bits : kFirstBits;
+            C = 1;
+        } else {
+            rb = bits - b0 < kPassBits ? bits - b0 : kPassBits;
+            C = kCols;
+        }
+        const int64_t tiles = table / ((int64_t)C << rb);
+        const size_t smem = (size_t)(8 << rb) * C;
+        if (cudaFuncSetAttribute(bps_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return GBN_ERR_CUDA;
+        if (launch_plain(bps_pass_kernel, dim3((unsigned)tiles), dim3(kTileThreads), smem, stream,
+                         scores, best, bset, m, b0, rb, first ? 1 : 0) != cudaSuccess)
+            return GBN_ERR_CUDA;
+        b0 += rb;
+        first = false;
+    }
+    return GBN_OK;
+}
+
+}  // namespace
+}  // namespace gbn
+
+using namespace gbn;
+
+extern "C" int givensbn_best_parents(const float* scores, int32_t m, float* best,
+                                     uint32_t* best_set, const givensbn_opts* opts) {
+    if (m < GBN_MIN_M || m > GBN_MAX_M) return GBN_ERR_M;
+    if (!scores || !best || !best_set) return GBN_ERR_NULL;
+    if (((uintptr_t)scores & 15u) || ((uintptr_t)best & 15u) || ((uintptr_t)best_set & 15u))
+        return GBN_ERR_ALIGN;
+    return run_bps(scores, m, best, best_set, static_cast<cudaStream_t>(opts ? opts->stream : nullptr));
+}
+
+extern "C" int givensbn_structure_search_workspace_size(int32_t m, size_t* bytes) {
+    if (!bytes) return GBN_ERR_NULL;
+    if (m < GBN_MIN_M || m > GBN_MAX_M) return GBN_ERR_M;
+    *bytes = search_layout(m).total;
+    return GBN_OK;
+}
+
+extern "C" int givensbn_structure_search(const float* scores, int32_t m, uint32_t* parents,
+                                         int32_t* order, double* total,
+                                         const givensbn_opts* opts) {
+    if (!opts) return GBN_ERR_NULL;
+    if (m < GBN_MIN_M || m > GBN_MAX_M) return GBN_ERR_M;
+    if (!scores || !parents || !total) return GBN_ERR_NULL;
+    if (((uintptr_t)scores & 15u) || ((uintptr_t)parents & 3u) || ((uintptr_t)order & 3u) ||
+        ((uintptr_t)total & 7u))
+        return GBN_ERR_ALIGN;
+    const SearchLayout L = search_layout(m);
+    if (!opts->workspace || opts->workspace_bytes < L.total) return GBN_ERR_WORKSPACE;
+    if ((uintptr_t)opts->workspace & 255u) return GBN_ERR_ALIGN;
+    char* ws = static_cast<char*>(opts->workspace);
+    cudaStream_t stream = static_cast<cudaStream_t>(opts->stream);
+    int rc;
+    float* best = reinterpret_cast<float*>(ws + L.off_best);
+    uint32_t* bset = reinterpret_cast<uint32_t*>(ws + L.off_set);
+    double* F = reinterpret_cast<double*>(ws + L.off_F);
+    uint8_t* sink = reinterpret_cast<uint8_t*>(ws + L.off_sink);
+    if ((rc = run_bps(scores, m, best, bset, stream))) return rc;
+    if (launch_plain(dp_init_kernel, dim3(1), dim3(1), 0, stream, F) != cudaSuccess)
+        return GBN_ERR_CUDA;
+    long long cnt = 1;  // C(m, p)
+    for (int p = 1; p <= m; ++p) {
+        cnt = cnt * (m - p + 1) / p;
+        const unsigned blocks = (unsigned)((cnt + 255) / 256);
+        if (launch_plain(dp_layer_kernel, dim3(blocks), dim3(256), 0, stream,
+                         (const float*)best, F, sink, (int)m, p, cnt) != cudaSuccess)
+            return GBN_ERR_CUDA;
+    }
+    return launch_rc(launch_plain(backtrack_kernel, dim3(1), dim3(1), 0, stream, (const double*)F,
+                                  (const uint8_t*)sink, (const uint32_t*)bset, (int)m, parents,
+                                  order, total));
+}

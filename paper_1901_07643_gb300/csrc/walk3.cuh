@@ -75,7 +75,7 @@ struct WalkArgs {
     size_t leaf_stride;
     int m, k, W, lanes;
     T alpha;                     // n ln 2
-    T lnn;                       // ln n
+    T lam;                       // penalty per parent (ln n for BIC, 2 for AIC)
     T nlnn;                      // n ln n
     unsigned long long* chk;     // check record (checked builds)
     unsigned long long* timing;  // role cycle counters (timing builds)
@@ -83,10 +83,10 @@ struct WalkArgs {
     size_t out_size;             // table elements
     int n_cwarps;                // consumer warps per CTA
     long long watchdog_ns;       // bound on every wait
+    int kmax;                    // families with more parents are not stored (m - 1: no bound)
+    int64_t cta0;                // global index of this launch's first sub-walk CTA (sharding)
 };
 
-// A wait inside the walk that lasts this long means the schedule is broken.
-constexpr long long kWatchdogNs = 2000000000ll;
 
 // Walk arguments of one dataset (host side).
 template <typename T>
@@ -101,14 +101,16 @@ inline WalkArgs<T> make_walk_args(const Plan& p, char* ws, void* out) {
     a.lanes = p.lanes;
     const double n = (double)p.n;
     a.alpha = (T)(n * 0.69314718055994530942);
-    a.lnn = (T)log(n);
+    a.lam = (T)p.lam;
     a.nlnn = (T)(n * log(n));
     a.chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
     a.timing = reinterpret_cast<unsigned long long*>(ws + p.off_status + kTimingOffset);
     a.status = reinterpret_cast<int*>(ws + p.off_status);
     a.out_size = (size_t)p.m << (p.m - 1);
     a.n_cwarps = p.n_bwarps;
-    a.watchdog_ns = kWatchdogNs;
+    a.watchdog_ns = p.watchdog_ns;
+    a.kmax = p.kmax;
+    a.cta0 = p.cta_begin;
     return a;
 }
 
@@ -278,8 +280,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
             smem_addr(bar))
         : "memory");
 }
-// One poll; a thread whose phase is not complete is suspended until it
-// completes or kSuspendNs pass, so a waiting warp issues almost nothing.
+// One poll that suspends: a thread whose phase is not complete is suspended
+// until it completes or about kSuspendNs pass, so a waiting warp issues
+// almost nothing.
 constexpr unsigned kSuspendNs = 20000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     uint32_t ok;
@@ -291,27 +294,45 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
+// One poll that returns at once.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], "
+        "%2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 __device__ __forceinline__ long long global_ns() {
     long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
 // Bounded wait for the phase with the given parity (false = the watchdog
-// expired; the clock is read every 64 polls).  Warp-uniform: every lane
+// expired).  The first poll returns at once; after it fails, the clock
+// starts and every later poll suspends (up to about kSuspendNs) and is
+// followed by a clock check, so a wait that is not complete within limit_ns
+// ends after about that long.  A bound below kSuspendNs cannot be resolved by
+// suspending polls: such a bound expires a wait whose phase is not complete
+// at its first poll (so a bound shorter than the producer's time for one tape
+// chunk makes a consumer's first wait expire).  Warp-uniform: every lane
 // polls (one instruction for the warp, the same phase seen by all lanes, each
 // lane's own acquire), so the loop has no divergent branch and no broadcast;
 // only the watchdog's status write is made by lane 0.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, unsigned parity, long long limit_ns,
                                           int* status) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = global_ns();
-    for (unsigned n = 1;; ++n) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((n & 63u) == 0 && global_ns() - t0 > limit_ns) {
-            if ((threadIdx.x & 31) == 0) atomicOr(status, GBN_STATUS_WATCHDOG);
-            return false;
+    if (mbar_test_wait(bar, parity)) return true;
+    if (limit_ns >= (long long)kSuspendNs) {
+        const long long t0 = global_ns();
+        for (;;) {
+            if (mbar_try_wait(bar, parity)) return true;
+            if (global_ns() - t0 > limit_ns) break;
         }
     }
+    if ((threadIdx.x & 31) == 0) atomicOr(status, GBN_STATUS_WATCHDOG);
+    return false;
 }
 
 // Timing builds (-DGBN_TIMING) add the cycles each role spends in total and
@@ -472,12 +493,14 @@ p_done:
 // One column replayed from the tape with straight-line code.  jj is the bit
 // of the column's free variable in the prefix masks (Q for a fixed variable:
 // never in a prefix), sh the shift that places the compressed prefix mask in
-// the table slot.  Returns false if a wait expired.
+// the table slot, kr the largest prefix length whose families are stored
+// (the in-degree bound less the lane's front-set size).  Returns false if a
+// wait expired.
 template <typename T, int Q, bool COV>
 __device__ __forceinline__ bool replay(const WalkArgs<T>& a, const typename Vec2T<T>::type* tape,
                                        uint64_t* full, unsigned par, T (&z)[Q], T cres, int ell,
                                        int jj, int sh,
-                                       OutT<T, COV>* base, T penb, bool on) {
+                                       OutT<T, COV>* base, T penb, bool on, int kr) {
     constexpr int N = StepTab<Q>::N;
     T w[Q + 1];
     w[Q] = cres;
@@ -490,7 +513,7 @@ __device__ __forceinline__ bool replay(const WalkArgs<T>& a, const typename Vec2
         constexpr unsigned pre = (1u << s) - 1u;
         const bool child = !((pre >> jj) & 1u);
         const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
-        emit_ptr<T, COV>(a, base, cT << sh, w[s], fma(T(s), a.lnn, penb), on && child);
+        emit_ptr<T, COV>(a, base, cT << sh, w[s], fma(T(s), a.lam, penb), on && child && s <= kr);
     });
     bool ok = true;
     static_for(std::make_integer_sequence<int, N>{}, [&](auto tc) {
@@ -510,11 +533,13 @@ __device__ __forceinline__ bool replay(const WalkArgs<T>& a, const typename Vec2
 #ifdef GBN_Q
         (void)pre;
         const unsigned cT = c_slots.v[t * (Q + 1) + jj];
-        emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, penb), on && cT != kNotChild);
+        emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lam, penb),
+                         on && cT != kNotChild && i + 1 <= kr);
 #else
         const bool child = !((pre >> jj) & 1u);
         const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
-        emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, penb), on && child && ok);
+        emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lam, penb),
+                         on && child && ok && i + 1 <= kr);
 #endif
     });
     return ok;
@@ -583,7 +608,7 @@ template <typename T, int Q, int H, bool COV>
 __device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
                                              const typename Vec2T<T>::type* tape, uint64_t* full,
                                              unsigned par, T (&z)[Q], T cres, int ell, int jj, int sh,
-                                             OutT<T, COV>* base, T penb, bool on) {
+                                             OutT<T, COV>* base, T penb, bool on, int kr) {
     static_assert(Q == GBN_Q, "the step table in constant memory is this unit's");
     static_assert(H >= 1 && Q - H >= 2, "blocks of at least two variables");
     constexpr int N = StepTab<Q>::N;
@@ -600,18 +625,18 @@ __device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
         constexpr unsigned pre = (1u << s) - 1u;
         const bool child = !((pre >> jj) & 1u);
         const unsigned cT = (pre & lm) | ((pre >> 1) & ~lm);
-        emit_ptr<T, COV>(a, base, cT << sh, w[s], fma(T(s), a.lnn, penb), on && child);
+        emit_ptr<T, COV>(a, base, cT << sh, w[s], fma(T(s), a.lam, penb), on && child && s <= kr);
     });
-    // one step at row i (absolute), tape step t; the compressed slot from the
-    // table.  After an expired wait the remaining stores may hold stale scores;
-    // the status word reports it.
+    // one step at row i (of the view), tape step t; the compressed slot from
+    // the table; kv the largest stored prefix length within the view.  After
+    // an expired wait the remaining stores may hold stale scores; the status
+    // word reports it.
     const uint16_t* slots = c_slots.v + jj;
     char* const base_b = reinterpret_cast<char*>(base);
     const unsigned stride = (unsigned)sizeof(OutT<T, COV>) << sh;
     const unsigned on_u = on ? 1u : 0u;
-    auto step = [&](auto& zz, auto& ww, int i_local, auto ic, int t, T pen_base, bool& ok) {
+    auto step = [&](auto& zz, auto& ww, int kv, auto ic, int t, T pen_base, bool& ok) {
         constexpr int i = decltype(ic)::value;
-        (void)i_local;
         (void)ok;
         const unsigned cT = slots[t * (Q + 1)];
         const auto cs = tape[(size_t)t * 32 + ell];
@@ -622,16 +647,16 @@ __device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
         const T wn = fma(yn, yn, ww[i + 2]);
         ww[i + 1] = wn;
         if constexpr (COV) {
-            emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, pen_base),
-                             on && cT != kNotChild);
+            emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lam, pen_base),
+                             on && cT != kNotChild && i + 1 <= kv);
         } else {
 #ifdef GBN_CHECKED
-            emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lnn, pen_base),
-                             on && cT != kNotChild);
+            emit_ptr<T, COV>(a, base, cT << sh, wn, fma(T(i + 1), a.lam, pen_base),
+                             on && cT != kNotChild && i + 1 <= kv);
 #else
             (void)base_b;
-            st_slot(base_b, stride, cT, fma(a.alpha, wk_log2(wn), fma(T(i + 1), a.lnn, pen_base)),
-                    on_u);
+            st_slot(base_b, stride, cT, fma(a.alpha, wk_log2(wn), fma(T(i + 1), a.lam, pen_base)),
+                    on_u & (unsigned)(i + 1 <= kv));
 #endif
         }
     };
@@ -647,11 +672,12 @@ __device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
         const int o = __popc(b);  // row shift of this block
         T zv[QB], wv[QB + 1];
         ViewCopy<QB, H>::template in<T, Q>(zv, wv, z, w, o);
-        const T penv = fma(T(o), a.lnn, penb);  // the o moved variables are parents throughout
+        const T penv = fma(T(o), a.lam, penb);  // the o moved variables are parents throughout
         static_for(std::make_integer_sequence<int, NBLK>{}, [&](auto tc) {
             constexpr int t = decltype(tc)::value;
             if constexpr (t % kChunk == 0) wait_for(t0 + t, ok);
-            step(zv, wv, 0, std::integral_constant<int, kSteps<QB>.row[t]>{}, t0 + t, penv, ok);
+            step(zv, wv, kr - o, std::integral_constant<int, kSteps<QB>.row[t]>{}, t0 + t, penv,
+                 ok);
         });
         ViewCopy<QB, H>::template out<T, Q>(zv, wv, z, w, o);
         t0 += NBLK;
@@ -671,7 +697,7 @@ __device__ __forceinline__ bool replay_split(const WalkArgs<T>& a,
                         static_for(std::make_integer_sequence<int, len>{}, [&](auto uc) {
                             constexpr int u = decltype(uc)::value;
                             constexpr int i = OO + len - 1 - u;  // absolute swap row
-                            step(z, w, 0, std::integral_constant<int, i>{}, t0 + u, penb, ok);
+                            step(z, w, kr, std::integral_constant<int, i>{}, t0 + u, penb, ok);
                         });
                     }
                 });
@@ -721,11 +747,15 @@ __device__ __forceinline__ void st_pair(char* base, unsigned stride, unsigned cT
         : "l"(addr), "f"(v.x), "f"(v.y), "r"(cT), "r"(on_xy), "r"(on_x));
 }
 
-template <int Q, int H>
+// KB: the bounded in-degree form.  kx is the largest prefix length whose
+// family of sub-walk x is stored (the bound less |F_x|); y's families have
+// one parent more, so at a prefix length where only x's family is within
+// the bound the 8-byte store becomes x's 4-byte store.
+template <int Q, int H, bool KB>
 __device__ __forceinline__ bool replay_pair(const WalkArgs<float>& a, const float4* tape,
                                             uint64_t* full, unsigned par, float2 (&z)[Q], float2 cres,
                                             int ell, int jj, int sh, char* base, float2 penb,
-                                            unsigned on_xy, unsigned on_x) {
+                                            unsigned on_xy, unsigned on_x, int kx) {
     static_assert(Q == GBN_Q, "the step tables in constant memory are this unit's");
     constexpr int N = StepTab<Q>::N;
     constexpr int last_chunk = (N - 1) / kChunk;
@@ -735,10 +765,20 @@ __device__ __forceinline__ bool replay_pair(const WalkArgs<float>& a, const floa
     w[Q] = cres;
 #pragma unroll
     for (int r = Q - 1; r >= 0; --r) w[r] = __ffma2_rn(z[r], z[r], w[r + 1]);
-    const float2 alpha2 = f2(a.alpha), lnn2 = f2(a.lnn);
+    const float2 alpha2 = f2(a.alpha), lnn2 = f2(a.lam);
     const unsigned stride = 4u << sh;
     const unsigned lm = (1u << jj) - 1u;
-    auto emit2 = [&](unsigned cT, float2 rss, float2 pen) {
+    (void)kx;
+    // pl: the family's prefix length within the view, kv: the largest one stored for x
+    auto emit2 = [&](unsigned cT, float2 rss, float2 pen, int pl, int kv) {
+        unsigned oxy = on_xy, ox = on_x;
+        if constexpr (KB) {  // y has one parent more than x (fixed variable 0)
+            const unsigned y_in = (unsigned)(pl + 1 <= kv), x_in = (unsigned)(pl <= kv);
+            ox = (on_x | (on_xy & (y_in ^ 1u))) & x_in;
+            oxy = on_xy & y_in;
+        }
+        (void)pl;
+        (void)kv;
         const float2 lg = make_float2(wk_log2(rss.x), wk_log2(rss.y));
         const float2 sc = __ffma2_rn(alpha2, lg, pen);
 #ifdef GBN_CHECKED
@@ -746,22 +786,22 @@ __device__ __forceinline__ bool replay_pair(const WalkArgs<float>& a, const floa
             const size_t e0 = (size_t)(base - reinterpret_cast<char*>(a.out)) / 4 +
                               (size_t)cT * (stride / 4);
             float* p = reinterpret_cast<float*>(base + (size_t)cT * stride);
-            if ((on_xy || on_x) && GBN_IN(a.chk, 332, e0, a.out_size)) p[0] = sc.x;
-            if (on_xy && GBN_IN(a.chk, 333, e0 + 1, a.out_size)) p[1] = sc.y;
-            if (on_xy && (e0 & 1)) GBN_IN(a.chk, 334, e0, 0);  // an 8-byte store must be aligned
+            if ((oxy || ox) && GBN_IN(a.chk, 332, e0, a.out_size)) p[0] = sc.x;
+            if (oxy && GBN_IN(a.chk, 333, e0 + 1, a.out_size)) p[1] = sc.y;
+            if (oxy && (e0 & 1)) GBN_IN(a.chk, 334, e0, 0);  // an 8-byte store must be aligned
         }
 #else
-        st_pair(base, stride, cT, sc, on_xy, on_x);
+        st_pair(base, stride, cT, sc, oxy, ox);
 #endif
     };
     static_for(std::make_integer_sequence<int, Q + 1>{}, [&](auto sc) {  // the roots' families
         constexpr int s = decltype(sc)::value;
         constexpr unsigned pre = (1u << s) - 1u;
         const unsigned cT = ((pre >> jj) & 1u) ? kNotChild : ((pre & lm) | ((pre >> 1) & ~lm));
-        emit2(cT, w[s], __ffma2_rn(f2(float(s)), lnn2, penb));
+        emit2(cT, w[s], __ffma2_rn(f2(float(s)), lnn2, penb), s, kx);
     });
     const uint16_t* slots = c_slots.v + jj;
-    auto step = [&](auto& zz, auto& ww, auto ic, int t, float2 pen_base) {
+    auto step = [&](auto& zz, auto& ww, auto ic, int t, float2 pen_base, int kv) {
         constexpr int i = decltype(ic)::value;
         const unsigned cT = slots[t * (Q + 1)];
         const float4 cs = tape[(size_t)t * 32 + ell];
@@ -774,7 +814,7 @@ __device__ __forceinline__ bool replay_pair(const WalkArgs<float>& a, const floa
         zz[i + 1] = yn;
         const float2 wn = __ffma2_rn(yn, yn, ww[i + 2]);
         ww[i + 1] = wn;
-        emit2(cT, wn, __ffma2_rn(f2(float(i + 1)), lnn2, pen_base));
+        emit2(cT, wn, __ffma2_rn(f2(float(i + 1)), lnn2, pen_base), i + 1, kv);
     };
     auto wait_for = [&](int t, bool& ok) {
         int c = (t + kChunk - 1) / kChunk;
@@ -792,7 +832,7 @@ __device__ __forceinline__ bool replay_pair(const WalkArgs<float>& a, const floa
         static_for(std::make_integer_sequence<int, NBLK>{}, [&](auto tc) {
             constexpr int t = decltype(tc)::value;
             if constexpr (t % kChunk == 0) wait_for(t0 + t, ok);
-            step(zv, wv, std::integral_constant<int, kSteps<QB>.row[t]>{}, t0 + t, penv);
+            step(zv, wv, std::integral_constant<int, kSteps<QB>.row[t]>{}, t0 + t, penv, kx - o);
         });
         ViewCopy<QB, H>::template out<float2, Q>(zv, wv, z, w, o);
         t0 += NBLK;
@@ -811,7 +851,7 @@ __device__ __forceinline__ bool replay_pair(const WalkArgs<float>& a, const floa
                             constexpr int u = decltype(uc)::value;
                             constexpr int i = OO + len - 1 - u;
                             if constexpr (i + 1 < Q)
-                                step(z, w, std::integral_constant<int, i>{}, t0 + u, penb);
+                                step(z, w, std::integral_constant<int, i>{}, t0 + u, penb, kx);
                         });
                     }
                 });
@@ -829,7 +869,7 @@ __device__ __forceinline__ bool replay_pair(const WalkArgs<float>& a, const floa
 // 2 (l & 15) and 2 (l & 15) + 1 (one 8-byte load).  The warp takes items
 // first, first + stride, ...; returns the number of items of the pair, or -1
 // when a wait expired.
-template <int Q>
+template <int Q, bool KB>
 __device__ __forceinline__ int consume_pair(const WalkArgs<float>& a, const float* __restrict__ rec0,
                                             const float* __restrict__ rec1, const float4* tape,
                                             uint64_t* full, unsigned par, int lane, int first,
@@ -839,7 +879,7 @@ __device__ __forceinline__ int consume_pair(const WalkArgs<float>& a, const floa
     const int nu = (a.k - 6) - __popcll(pc);  // fixed variables above 5 outside F
     const int nitems = Q + nu + 3 + 1;
     char* out = reinterpret_cast<char*>(a.out);
-    const float lnn = a.lnn;
+    const float lnn = a.lam;
     // penalty bases of the two sub-walks, rounded as the single walk rounds them
     auto pen2 = [&](uint64_t Fx) {
         const float c0 = float(__popcll(Fx));
@@ -893,8 +933,10 @@ __device__ __forceinline__ int consume_pair(const WalkArgs<float>& a, const floa
             const uint64_t lowmask = (1ull << v) - 1ull;
             slot = ((size_t)v << (a.m - 1)) + ((Fx & lowmask) | ((Fx >> (v + 1)) << v));
         }
-        const bool ok = replay_pair<Q, H>(a, tape, full, par, z, cres, pl, jj, sh, out + slot * 4,
-                                          pen2((pc << 6) | ((uint64_t)pl << 1)), on_xy, on_x);
+        const uint64_t Fx = (pc << 6) | ((uint64_t)pl << 1);
+        const bool ok = replay_pair<Q, H, KB>(a, tape, full, par, z, cres, pl, jj, sh,
+                                              out + slot * 4, pen2(Fx), on_xy, on_x,
+                                              KB ? a.kmax - __popcll(Fx) : 0);
         if (!ok) return -1;
     }
     return nitems;
@@ -967,15 +1009,17 @@ __device__ __forceinline__ int consume(const WalkArgs<T>& a, const T* __restrict
             base = reinterpret_cast<OutT<T, COV>*>(a.out) + ((size_t)v << (a.m - 1)) +
                    (size_t)((F & lowmask) | ((F >> (v + 1)) << v));
         }
-        const T penb = fma(T(__popcll(Fhi | (uint64_t)ell)), a.lnn, -a.nlnn);
+        const int nF = __popcll(Fhi | (uint64_t)ell);
+        const T penb = fma(T(nF), a.lam, -a.nlnn);
+        const int kr = a.kmax - nF;
         bool ok;
 #ifdef GBN_Q
         if constexpr (split_levels(Q) > 0)
             ok = replay_split<T, Q, split_levels(Q), COV>(a, tape, full, par, z, cres, ell, jj, sh,
-                                                        base, penb, on);
+                                                        base, penb, on, kr);
         else
 #endif
-            ok = replay<T, Q, COV>(a, tape, full, par, z, cres, ell, jj, sh, base, penb, on);
+            ok = replay<T, Q, COV>(a, tape, full, par, z, cres, ell, jj, sh, base, penb, on, kr);
         if (!ok) return -1;
     }
     GBN_TIMER_FLUSH(a.timing, 1)
@@ -1009,13 +1053,16 @@ __device__ __forceinline__ void walk_body(const WalkArgs<T>& a, uint64_t cta) {
     if (threadIdx.x < S::chunks) mbar_init(&full[threadIdx.x], 1);
     for (int c = threadIdx.x + blockDim.x; c < S::chunks; c += blockDim.x) mbar_init(&full[c], 1);
     __syncthreads();
-    const uint64_t Fhi = cta << a.W;
+    // cta: this launch's CTA (leaf record); g: its global index (front set bits)
+    const uint64_t g = cta + (uint64_t)a.cta0;
+    if (__popcll(g) > a.kmax) return;  // every family of these sub-walks has too many parents
+    const uint64_t Fhi = g << a.W;
     const T* rec = a.leaves + (size_t)cta * a.leaf_stride;
     if (warp == 0)
         produce<T, Q>(a, c_steps, rec, smem + S::off_tape, full, lane, lane < a.lanes);
     else
         consume<T, Q, COV>(a, rec, reinterpret_cast<const typename Vec2T<T>::type*>(smem + S::off_tape),
-                           full, 0u, lane, warp - 1, a.n_cwarps, cta, Fhi);
+                           full, 0u, lane, warp - 1, a.n_cwarps, g, Fhi);
 }
 
 template <typename T, int Q, bool COV>
@@ -1040,7 +1087,12 @@ __global__ void __launch_bounds__(32 * (1 + kMaxConsumerWarps)) walk_kernel_b(co
 constexpr int kPairConsumerWarps = 8;
 constexpr int kPairThreads = 32 * (2 + kPairConsumerWarps);
 constexpr size_t kPairMaxSmem = 160 * 1024;  // the tape of Q = 9 does not fit
-template <int Q>
+// pc: the pair of this launch (leaf records 2 pc, 2 pc + 1).  GEN, the
+// general form, serves a bounded in-degree (KB stores) and shards: the pair's
+// global index (its front set bits) is pc + cta0 / 2, cta0 being even.  The
+// plain form (the whole table, no bound) takes pc itself, which the compiler
+// can re-read from the block index instead of keeping it in a register.
+template <int Q, bool GEN>
 __device__ __forceinline__ void walk_pair_body(const WalkArgs<float>& a, uint64_t pc) {
     extern __shared__ __align__(16) unsigned char smem[];
     using S = SmemP<Q>;
@@ -1049,19 +1101,24 @@ __device__ __forceinline__ void walk_pair_body(const WalkArgs<float>& a, uint64_
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::off_bar);
     for (int c = threadIdx.x; c < S::chunks; c += blockDim.x) mbar_init(&full[c], 2);
     __syncthreads();
+    uint64_t gpc = pc;
+    if constexpr (GEN) {
+        gpc += (uint64_t)a.cta0 >> 1;
+        if (__popcll(gpc) > a.kmax) return;  // every family here has too many parents
+    }
     const float* rec0 = a.leaves + (size_t)(2 * pc) * a.leaf_stride;
     const float* rec1 = rec0 + a.leaf_stride;
     if (warp < 2)
         produce<float, Q, true>(a, c_steps, warp ? rec1 : rec0, smem + S::off_tape, full, lane,
                                 true, pair_tape_word(warp, lane));
     else
-        consume_pair<Q>(a, rec0, rec1, reinterpret_cast<const float4*>(smem + S::off_tape), full,
-                        0u, lane, warp - 2, (int)(blockDim.x >> 5) - 2, pc);
+        consume_pair<Q, GEN>(a, rec0, rec1, reinterpret_cast<const float4*>(smem + S::off_tape),
+                             full, 0u, lane, warp - 2, (int)(blockDim.x >> 5) - 2, gpc);
 }
 
-template <int Q>
+template <int Q, bool GEN>
 __global__ void __launch_bounds__(kPairThreads, Q >= 8 ? 1 : 3) walk_kernel_pair(const WalkArgs<float> a) {
-    walk_pair_body<Q>(a, blockIdx.x);
+    walk_pair_body<Q, GEN>(a, blockIdx.x);
 }
 
 // A batch in which every dataset takes the paired walk (every CTA count is
@@ -1072,7 +1129,7 @@ __global__ void __launch_bounds__(kPairThreads, Q >= 8 ? 1 : 3) walk_kernel_pair
     int64_t local;
     const int d = batch_locate(v, v.cta_prefix, 2 * (int64_t)blockIdx.x, local);
     const WalkArgs<float> a = static_cast<const WalkArgs<float>*>(v.walk_args)[d];
-    walk_pair_body<Q>(a, (uint64_t)local >> 1);
+    walk_pair_body<Q, false>(a, (uint64_t)local >> 1);
 }
 
 // Whether a launch takes the paired walk: FP32 scores, full warps of
@@ -1158,9 +1215,9 @@ __global__ void __launch_bounds__(ring_threads<Q, PAIR>(),
             int n;
             if constexpr (PAIR) {
                 const float* rec0 = a.leaves + (size_t)(2 * u) * a.leaf_stride;
-                n = consume_pair<Q>(a, rec0, rec0 + a.leaf_stride,
-                                    reinterpret_cast<const float4*>(tb), fb, par, lane, first, NC,
-                                    (uint64_t)u);
+                n = consume_pair<Q, false>(a, rec0, rec0 + a.leaf_stride,
+                                           reinterpret_cast<const float4*>(tb), fb, par, lane,
+                                           first, NC, (uint64_t)u);
             } else {
                 const float* rec = a.leaves + (size_t)u * a.leaf_stride;
                 n = consume<float, Q, false>(a, rec, reinterpret_cast<const float2*>(tb), fb, par,
@@ -1189,8 +1246,8 @@ int launch_walk_ring(const WalkArgs<float>& a, int64_t n_units, cudaStream_t str
         return GBN_ERR_CUDA;
     if (per_sm < 1) return GBN_ERR_CUDA;
     const int64_t blocks = std::min<int64_t>(n_units, (int64_t)sms * per_sm);
-    walk_ring_kernel<Q, PAIR><<<(unsigned)blocks, threads, smem, stream>>>(a, n_units);
-    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+    return launch_rc(launch_plain(walk_ring_kernel<Q, PAIR>, dim3((unsigned)blocks), dim3(threads),
+                                  smem, stream, a, n_units));
 }
 
 // Which FP32 score walk a launch takes (full warps of sub-walks, W = 5):
@@ -1202,38 +1259,48 @@ constexpr int fp32_walk_form() {
     return (Q <= 6 && ring_walk_compiled<Q, true>()) ? 3 : 1;
 }
 
+template <int Q, bool GEN>
+int launch_walk_pair(const WalkArgs<float>& a, int64_t n_cta, cudaStream_t stream) {
+    const size_t smem_p = SmemP<Q>::bytes;
+    if (cudaFuncSetAttribute(walk_kernel_pair<Q, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_p) != cudaSuccess)
+        return GBN_ERR_CUDA;
+    const int ncw = a.n_cwarps < kPairConsumerWarps ? a.n_cwarps : kPairConsumerWarps;
+    return launch_rc(launch_plain(walk_kernel_pair<Q, GEN>, dim3((unsigned)(n_cta / 2)),
+                                  dim3(32 * (2 + ncw)), smem_p, stream, a));
+}
+
+// n_cta: the sub-walk CTAs of this launch (a.cta0 is the global index of the
+// first; even whenever n_cta is).
 template <typename T, int Q, bool COV>
 int launch_walk_q(const WalkArgs<T>& a, int64_t n_cta, cudaStream_t stream) {
     const size_t smem = Smem<T, Q>::bytes;
     if (a.n_cwarps < 1 || a.n_cwarps > kMaxConsumerWarps) return GBN_ERR_Q;
+    if (n_cta < 1) return GBN_OK;
+    // the general forms for a bounded in-degree or a shard of the table
+    const bool general = a.kmax < a.m - 1 || a.cta0 != 0;
     if constexpr (std::is_same<T, float>::value && !COV) {
         constexpr int form = fp32_walk_form<Q>();
         const bool full_warps = a.W == 5 && a.lanes == 32;
-        const bool pairs = full_warps && n_cta >= 2 && n_cta % 2 == 0;
+        const bool pairs = full_warps && n_cta >= 2 && n_cta % 2 == 0 && a.cta0 % 2 == 0;
         if constexpr (form == 3) {
-            if (pairs) return launch_walk_ring<Q, true>(a, n_cta / 2, stream);
+            if (pairs && !general) return launch_walk_ring<Q, true>(a, n_cta / 2, stream);
         }
         if constexpr (form >= 2) {
-            if (full_warps) return launch_walk_ring<Q, false>(a, n_cta, stream);
+            if (full_warps && !general) return launch_walk_ring<Q, false>(a, n_cta, stream);
         }
-    }
-    if constexpr (pair_walk_compiled<T, Q, COV>()) {
-        if (fp32_walk_form<Q>() == 1 && a.W == 5 && a.lanes == 32 && n_cta >= 2 && n_cta % 2 == 0) {
-            const size_t smem_p = SmemP<Q>::bytes;
-            if (cudaFuncSetAttribute(walk_kernel_pair<Q>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_p) != cudaSuccess)
-                return GBN_ERR_CUDA;
-            const int ncw = a.n_cwarps < kPairConsumerWarps ? a.n_cwarps : kPairConsumerWarps;
-            walk_kernel_pair<Q><<<(unsigned)(n_cta / 2), 32 * (2 + ncw), smem_p, stream>>>(a);
-            return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+        if constexpr (pair_walk_compiled<T, Q, COV>()) {
+            if (pairs) {
+                if (general) return launch_walk_pair<Q, true>(a, n_cta, stream);
+                if (form == 1) return launch_walk_pair<Q, false>(a, n_cta, stream);
+            }
         }
     }
     if (cudaFuncSetAttribute(walk_kernel<T, Q, COV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return GBN_ERR_CUDA;
-    walk_kernel<T, Q, COV><<<(unsigned)n_cta, 32 * (1 + a.n_cwarps), smem, stream>>>(a);
-    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+    return launch_rc(launch_plain(walk_kernel<T, Q, COV>, dim3((unsigned)n_cta),
+                                  dim3(32 * (1 + a.n_cwarps)), smem, stream, a));
 }
 
 template <typename T, int Q, bool COV>
@@ -1248,15 +1315,15 @@ int launch_walk_batched_q(const BatchView& v, int64_t total_cta, int n_cwarps, c
                                      (int)smem_p) != cudaSuccess)
                 return GBN_ERR_CUDA;
             const int ncw = n_cwarps < kPairConsumerWarps ? n_cwarps : kPairConsumerWarps;
-            walk_kernel_pair_b<Q><<<(unsigned)(total_cta / 2), 32 * (2 + ncw), smem_p, stream>>>(v);
-            return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+            return launch_rc(launch_plain(walk_kernel_pair_b<Q>, dim3((unsigned)(total_cta / 2)),
+                                          dim3(32 * (2 + ncw)), smem_p, stream, v));
         }
     }
     if (cudaFuncSetAttribute(walk_kernel_b<T, Q, COV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return GBN_ERR_CUDA;
-    walk_kernel_b<T, Q, COV><<<(unsigned)total_cta, 32 * (1 + n_cwarps), smem, stream>>>(v);
-    return cudaGetLastError() == cudaSuccess ? GBN_OK : GBN_ERR_CUDA;
+    return launch_rc(launch_plain(walk_kernel_b<T, Q, COV>, dim3((unsigned)total_cta),
+                                  dim3(32 * (1 + n_cwarps)), smem, stream, v));
 }
 
 }  // namespace gbn

@@ -139,20 +139,69 @@ def _device_gather(table: torch.Tensor, slots: np.ndarray) -> np.ndarray:
     return table[idx].double().cpu().numpy()
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_workload_m26_sampled(precision):
-    """The benchmark's launch configuration (automatic q) on the m=26 workload."""
+def _collinear_pairs(X, thresh=0.99):
+    m = X.shape[1]
+    C = np.corrcoef(X, rowvar=False)
+    return [(a, b) for a in range(m) for b in range(m) if a != b and abs(C[a, b]) > thresh]
+
+
+def _every_collinear_family(X):
+    """Every family whose child is one column of a near-collinear pair and whose parent set
+    holds the other: 2^(m-2) parent sets per ordered pair."""
+    m = X.shape[1]
+    child, mask = [], []
+    for a, b in _collinear_pairs(X):
+        rest = np.arange(1 << (m - 2), dtype=np.uint64)
+        lo, hi = min(a, b), max(a, b)
+        # spread the (m-2)-bit counter over the variables other than a and b
+        full = (rest & np.uint64((1 << lo) - 1)) | ((rest >> np.uint64(lo)) << np.uint64(lo + 1))
+        full = (full & np.uint64((1 << hi) - 1)) | ((full >> np.uint64(hi)) << np.uint64(hi + 1))
+        child.append(np.full(len(rest), a, np.int32))
+        mask.append(full | np.uint64(1 << b))
+    return np.concatenate(child), np.concatenate(mask)
+
+
+@pytest.fixture(scope="module")
+def m26_reference():
+    """Oracle values on the m=26 workload, shared by the FP32 and FP64 checks: 2^20 seeded
+    random families and every collinear-pair family (R0-reduced oracle, pinned to the direct
+    one), and 2^17 seeded random families plus 1000 collinear ones solved directly on Xc."""
     w = synthetic.LARGE_M26
     X = synthetic.workload_sample(w)
+    child_r, mask_r = _sample(w.m, 1 << 20, 2600)
+    child_c, mask_c = _every_collinear_family(X)
+    assert len(child_c) >= 1 << 24
+    child = np.concatenate([child_r, child_c])
+    mask = np.concatenate([mask_r, mask_c])
+    _, ref_red = oracle.scores_sampled(X, child, mask, reduced=True)
+    extra = _collinear_families(X, 1000, 26)
+    child_d, mask_d = _sample(w.m, 1 << 17, 2601, extra)
+    _, ref_dir = oracle.scores_sampled(X, child_d, mask_d)
+    return {"X": X, "w": w, "red": (child, mask, ref_red), "dir": (child_d, mask_d, ref_dir)}
+
+
+def _slots_np(child, mask, m):
+    """idx(c,S) = c 2^(m-1) + compress(S, c), vectorised."""
+    c = child.astype(np.uint64)
+    low = mask & ((np.uint64(1) << c) - np.uint64(1))
+    high = (mask >> (c + np.uint64(1))) << c
+    return ((c << np.uint64(m - 1)) + (low | high)).astype(np.int64)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_workload_m26_sampled(precision, m26_reference):
+    """The benchmark's launch configuration (automatic q) on the m=26 workload, compared
+    element by element with the oracle on 2^20 + 2^17 seeded families and on every family
+    of a near-collinear pair (child one column, parents holding the other)."""
+    ref = m26_reference
+    w, X = ref["w"], ref["X"]
     table = _gpu(X, precision=precision)
     assert table.numel() == 26 << 25
-    extra = _collinear_families(X, 1000, 26)
-    child, mask = _sample(w.m, 3000, 260 + precision, extra)
-    _, ref = oracle.scores_sampled(X, child, mask)
-    got = _device_gather(table, _slots(child, mask, w.m))
-    _check(got, ref, w.n, TOL[precision])
-    # every slot written, none non-finite
-    assert bool(torch.isfinite(table).all())
+    assert bool(torch.isfinite(table).all())  # every slot written, none non-finite
+    for key in ("red", "dir"):
+        child, mask, want = ref[key]
+        got = _device_gather(table, _slots_np(child, mask, w.m))
+        _check(got, want, w.n, TOL[precision])
     del table
     torch.cuda.empty_cache()
 

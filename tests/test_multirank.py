@@ -70,3 +70,41 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def _shard_rank_main(rank, port, out_dir, m, q):
+    """Each rank takes its shard of one m-variable table and lists the slots it writes
+    (families (c, S) whose sub-walk CTA (S & (2^k-1)) >> W is in the shard's range); the
+    ranks exchange the lists and check that they are disjoint and cover the table."""
+    import numpy as np
+    from paper_1901_07643_gb300 import binding
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=2)
+    try:
+        k, W, b, e = binding.shard_range(1000, m, (rank, 2), q=q)
+        half = 1 << (m - 1)
+        idx = np.arange(m * half, dtype=np.int64)
+        c = idx // half
+        comp = idx % half
+        S = (comp & ((1 << c) - 1)) | ((comp >> c) << (c + 1))
+        g = (S & ((1 << k) - 1)) >> W
+        mine = torch.from_numpy(((g >= b) & (g < e)).astype(np.uint8))
+        both = [torch.zeros_like(mine) for _ in range(2)]
+        dist.all_gather(both, mine)
+        total = both[0].int() + both[1].int()
+        with open(os.path.join(out_dir, f"s{rank}.json"), "w") as f:
+            json.dump([int(total.min()), int(total.max()), int(mine.sum())], f)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("m,q", [(16, 6), (13, 7)])
+def test_two_rank_shards_cover_the_table_once(tmp_path, m, q):
+    mp.start_processes(_shard_rank_main, args=(_free_port(), str(tmp_path), m, q), nprocs=2,
+                       start_method="spawn")
+    counts = []
+    for rank in range(2):
+        lo, hi, cnt = json.load(open(tmp_path / f"s{rank}.json"))
+        assert lo == 1 and hi == 1
+        counts.append(cnt)
+    assert sum(counts) == m << (m - 1)  # (13, 7) has one CTA pair: shard 0 is empty

@@ -268,3 +268,80 @@ def test_planted_mistakes_are_caught(code):
     finally:
         oracle.set_mutation(0)
     assert not all(results), f"mutation {code} passed every pin"
+
+
+def _pin_penalised_scores(X, lam):
+    """The penalised score against -2 * (Gaussian profile log-likelihood, scipy) + |S| * lam."""
+    n, m = X.shape
+    Xc = X - X.mean(0)
+    _, sc = oracle.scores(X, nthreads=2, penalty=lam)
+    for c, S, mask in _families(m):
+        y = Xc[:, c]
+        e = y - Xc[:, list(S)] @ np.linalg.lstsq(Xc[:, list(S)], y, rcond=None)[0] if S else y
+        sigma = np.sqrt(float(e @ e) / n)
+        minus2ll = -2.0 * stats.norm.logpdf(e, scale=sigma).sum()
+        want = minus2ll - n * np.log(2 * np.pi) - n + len(S) * lam
+        if abs(sc[oracle.table_index(c, mask, m)] - want) > 1e-8 * max(1.0, abs(want)):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("lam", [2.0, 0.0, 7.5])
+def test_penalised_scores_are_gaussian_information_criteria(lam):
+    assert _pin_penalised_scores(SMALL, lam)
+
+
+def _pin_coefficients(X, count=200, seed=0):
+    """Coefficients and intercept against LAPACK lstsq on the UNcentred data with a column of
+    ones (a different formulation of the same regression), and the RSS of that fit."""
+    n, m = X.shape
+    rng = np.random.default_rng(seed)
+    child = rng.integers(0, m, count).astype(np.int32)
+    mask = np.array([int(rng.integers(0, 1 << m)) & ~(1 << int(c)) for c in child], np.uint64)
+    beta, rss = oracle.coefficients(X, child, mask, nthreads=2)
+    for i, (c, S) in enumerate(zip(child, mask)):
+        cols = [v for v in range(m) if (int(S) >> v) & 1]
+        A = np.column_stack([X[:, cols], np.ones(n)])
+        sol = np.linalg.lstsq(A, X[:, c], rcond=None)[0]
+        e = X[:, c] - A @ sol
+        want = np.zeros(m + 1)
+        want[cols] = sol[:-1]
+        want[m] = sol[-1]
+        if np.max(np.abs(beta[i] - want) / np.maximum(np.abs(want), 1.0)) > 1e-9:
+            return False
+        if abs(rss[i] - float(e @ e)) > 1e-9 * float(e @ e):
+            return False
+    return True
+
+
+def test_coefficients_against_lstsq_with_intercept():
+    assert _pin_coefficients(synthetic.sem_sample(8, 60, 0.4, 21))
+    assert _pin_coefficients(synthetic.sem_sample(12, 300, 0.3, 22) + 5.0, seed=1)
+
+
+def test_coefficients_of_an_exact_linear_model():
+    """y = 3 + 2 x0 - x2 exactly: the coefficients are recovered, RSS is zero."""
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((40, 4))
+    X[:, 3] = 3.0 + 2.0 * X[:, 0] - X[:, 2]
+    beta, rss = oracle.coefficients(X, [3], [0b101])
+    np.testing.assert_allclose(beta[0], [2.0, 0.0, -1.0, 0.0, 3.0], atol=1e-12)
+    assert rss[0] < 1e-20
+
+
+def test_coefficients_with_dependent_parents_are_nan():
+    X = synthetic.sem_sample(5, 40, 0.4, 23)
+    X[:, 4] = X[:, 1]
+    beta, rss = oracle.coefficients(X, [0], [(1 << 1) | (1 << 4)])
+    assert np.isnan(beta[0, 1]) and np.isnan(beta[0, 4]) and np.isfinite(rss[0])
+
+
+def test_sampled_reduced_equals_direct():
+    X = synthetic.sem_sample(14, 400, 0.3, 24)
+    rng = np.random.default_rng(3)
+    child = rng.integers(0, 14, 3000).astype(np.int32)
+    mask = np.array([int(rng.integers(0, 1 << 14)) & ~(1 << int(c)) for c in child], np.uint64)
+    r1, s1 = oracle.scores_sampled(X, child, mask)
+    r2, s2 = oracle.scores_sampled(X, child, mask, reduced=True)
+    np.testing.assert_allclose(r2, r1, rtol=1e-10)
+    np.testing.assert_allclose(s2, s1, rtol=0, atol=1e-8)
