@@ -469,7 +469,7 @@ def _search_leg(table, m, flush, args):
         ms_bp.append(e[2].elapsed_time(e[3]))
     del best, bset, ws
     slots = m << (m - 1)
-    passes = 1 + -(-max(0, (m - 1) - 12) // 9)
+    passes = 1 + -(-max(0, (m - 1) - 12) // 7)
     bp_bytes = slots * (4 + 8) + (passes - 1) * slots * 16
     t_bp = statistics.median(ms_bp)
     peak, kind = _peak_hbm()
@@ -480,6 +480,12 @@ def _search_leg(table, m, flush, args):
                                       "frac": bp_bytes / (t_bp / 1e3) / 1e9 / peak,
                                       "algorithmic_bytes": bp_bytes, "peak_kind": kind},
             "network_score": total, "edges": int(sum(bin(p).count("1") for p in parents))}
+
+
+def rotation_flops(m):
+    """T(m) = 3m 2^m + 6 2^m - 3m^2 - 9m - 6: the flops of the Givens walk's rotations for m
+    variables (the complexity count of Sec. 5, Table 1)."""
+    return 3 * m * 2 ** m + 6 * 2 ** m - 3 * m * m - 9 * m - 6
 
 
 def _aggregate(total_ms, fam, steps, world, device):
@@ -541,6 +547,14 @@ def run_ours(args):
         gathered["families"] = _error_sample(X, w.m, 1 << 18)
         slots_t = torch.from_numpy(_slots(*gathered["families"], w.m)).to(dev)
 
+    peaks = None
+    try:  # measured FMA throughput: the FP64 walk's compute roofline
+        f32, f64 = binding.pipe_peaks(local)
+        peaks = {"fp32_tflops": f32, "fp64_tflops": f64,
+                 "how": "independent FMA chains on every SM, best of 3 launches (CUDA events)"}
+    except Exception as e:  # noqa: BLE001 - reported, not fatal
+        peaks = {"error": str(e)}
+
     fn32, out32, ws32, q32, cw32 = make(0)
     for _ in range(max(args.warmup, 0)):
         fn32([torch.cuda.Event(enable_timing=True) for _ in range(4)])
@@ -579,6 +593,16 @@ def run_ours(args):
                 "walk_ms": statistics.mean(w64),
                 "q": q64 or binding.auto_q(w.m, 1), "consumer_warps": cw64 or None,
                 "dtype": "f64", "steps": k64}
+        if peaks and "fp64_tflops" in peaks:
+            wsec = statistics.mean(w64) / 1e3
+            ach = rotation_flops(w.m) / wsec / 1e12
+            fp64["roofline"] = {
+                "bound": "fp64", "achieved": ach, "peak": peaks["fp64_tflops"],
+                "unit": "TFLOP/s", "frac": ach / peaks["fp64_tflops"], "peak_kind": "measured",
+                "algorithmic_flops": rotation_flops(w.m),
+                "note": "rotation flops T(m) of Sec. 5 only; each family also takes an FP64 "
+                        "logarithm (a software routine) that the count leaves out",
+                "hbm_frac": 8 * fam / wsec / 1e9 / _peak_hbm()[0]}
         if want_errors:
             gathered["fp64"] = out64[slots_t].cpu().numpy()
         del out64, ws64
@@ -617,6 +641,7 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": algo_bytes},
         "cpu_baseline": cpu,
         "errors": errors,
+        "pipe_peaks": peaks,
         "autotune": tuned or None,
         "e2e": e2e,
         "clocks": clocks,

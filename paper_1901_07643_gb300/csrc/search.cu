@@ -14,8 +14,8 @@
 //      variable.
 // Step 1 is a subset-minimum transform of each child's 2^(m-1) block (one bit
 // of the compressed parent mask at a time; a block of bits per pass through a
-// shared-memory tile, so HBM is read and written once per pass, 3 passes at
-// m = 26); step 2 runs one launch per subset size, threads over the subsets of
+// shared-memory tile, so HBM is read and written once per pass: 12 bits in
+// the first, 7 in each later one, 3 passes at m = 26); step 2 runs one launch per subset size, threads over the subsets of
 // that size (unranked in the combinatorial number system), in FP64.
 // Ties: the smaller candidate set (the subset) in step 1, the smallest sink in
 // step 2, so the result is deterministic.
@@ -27,8 +27,9 @@ namespace gbn {
 namespace {
 
 constexpr int kFirstBits = 12;  // bits of the first (contiguous) pass: 4096-entry tiles
-constexpr int kPassBits = 9;    // bits of each later pass: 512 rows x 8 columns
-constexpr int kCols = 8;        // consecutive entries per row of a strided tile (32 bytes)
+constexpr int kPassBits = 7;    // bits of each later pass: 128 rows x 32 columns
+constexpr int kCols = 32;       // consecutive entries per row of a strided tile (128 bytes:
+                                // a whole cache line, where 32-byte rows left DRAM at 1/8)
 constexpr int kTileThreads = 512;
 
 // One tile in shared memory: R rows (stride `rs` apart in the child block)
