@@ -421,21 +421,39 @@ def _extras(dev, flush, args):
     del tbl, ws, graph
     Gs, w = synthetic.gradient_workload()
     Gd = [torch.from_numpy(X).to(dev) for X in Gs]
-    wt = torch.from_numpy(w).to(dev)
-    wsb = torch.empty(binding.backward_workspace_size(Gs[0].shape[0], Gs[0].shape[1]),
+    wt = torch.from_numpy(w).to(dev).float()
+    fam = len(Gd) * (16 << 15)
+    wsb = torch.empty(binding.backward_batched_workspace_size(Gd), dtype=torch.uint8, device=dev)
+    grads = [torch.empty_like(X) for X in Gd]
+    for _ in range(2):
+        binding.score_all_families_backward_batched(Gd, wt, workspace=wsb, grads=grads)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(5):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        binding.score_all_families_backward_batched(Gd, wt, workspace=wsb, grads=grads)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = statistics.median(ms)
+    del wsb
+    ws1 = torch.empty(binding.backward_workspace_size(Gs[0].shape[0], Gs[0].shape[1]),
                       dtype=torch.uint8, device=dev)
-    binding.score_all_families_backward(Gd[0], wt, workspace=wsb, check=False)
+    binding.score_all_families_backward(Gd[0], wt, workspace=ws1, check=False)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for X in Gd:
-        binding.score_all_families_backward(X, wt, workspace=wsb, check=False)
+        binding.score_all_families_backward(X, wt, workspace=ws1, check=False)
     b.record()
     torch.cuda.synchronize()
-    t = a.elapsed_time(b)
-    fam = len(Gd) * (16 << 15)
+    t1 = a.elapsed_time(b)
     out["adjoint"] = {"workload": "gradient_64 (m=16, n=2000)", "datasets": len(Gd),
                       "ms_total": t, "value": fam / (t / 1e3), "unit": "family adjoints/s",
+                      "launch": "score_all_families_backward_batched (one call, 64 datasets)",
+                      "ms_total_64_single_calls": t1,
                       "dtype": "f32 walk, f64 accumulation"}
     return out
 

@@ -225,6 +225,26 @@ int givensbn_backward_workspace_size(int64_t n, int32_t m, const givensbn_opts* 
                                      size_t* bytes);
 
 /*
+ * score_all_families_backward for B datasets of uneven size in four launch groups: the R0
+ * stage of every dataset (as in score_all_families_batched), one launch of the adjoint walk
+ * over all datasets' sub-walks, one reduction and one gradient launch.  Each gradient is
+ * bit-identical to the single-dataset call's (the same sub-walks on the same warps, sums in
+ * the same order).  Batching is an engineering addition; the paper has no gradient.
+ *   Xs, ns, ms  as for score_all_families_batched
+ *   weights     host array of B device pointers, weights of dataset b in its table layout
+ *               (m_b 2^(m_b-1) entries; float for precision 0, double for 1), 16-byte aligned
+ *   grads       host array of B device pointers, n_b x m_b FP64 outputs
+ *   opts        host; opts->q is the backward sub-walk size (0 = m - 10 per dataset);
+ *               workspace >= givensbn_backward_batched_workspace_size()
+ * Returns 0 or GBN_ERR_*; per-dataset status words are not read by givensbn_status.
+ */
+int score_all_families_backward_batched(const double* const* Xs, const int64_t* ns,
+                                        const int32_t* ms, int32_t B, const void* const* weights,
+                                        double* const* grads, const givensbn_opts* opts);
+int givensbn_backward_batched_workspace_size(const int64_t* ns, const int32_t* ms, int32_t B,
+                                             const givensbn_opts* opts, size_t* bytes);
+
+/*
  * score_all_families without a workspace and without any allocation.  The
  * paper has no counterpart: this is an engineering variant for callers that
  * cannot allocate device memory when they call (a host runtime whose pool

@@ -10,5 +10,6 @@ from .binding import (GivensBNError, all_family_scores, auto_q, autotune,  # noq
                       autotune_batched, batch_offsets, backward_workspace_size, best_parents,
                       batched_workspace_size, family_coefficients, load, plan_choice,
                       score_all_families, score_all_families_batched,
-                      score_all_families_backward, score_all_families_noalloc, shard_range,
+                      score_all_families_backward, score_all_families_backward_batched,
+                      score_all_families_noalloc, shard_range,
                       strerror, structure_search, workspace_size)

@@ -109,6 +109,8 @@ def load():
             lib.givensbn_family_coefficients.argtypes = [P, i64, i32, P, P, i64, P, P, OP]
             lib.givensbn_best_parents.argtypes = [P, i32, P, P, OP]
             lib.givensbn_pipe_peaks.argtypes = [P, P, DP, DP]
+            lib.score_all_families_backward_batched.argtypes = [P, P, P, i32, P, P, OP]
+            lib.givensbn_backward_batched_workspace_size.argtypes = [P, P, i32, OP, SZP]
             lib.givensbn_structure_search_workspace_size.argtypes = [i32, SZP]
             lib.givensbn_structure_search.argtypes = [P, i32, P, P, P, OP]
             _lib = lib
@@ -603,3 +605,56 @@ def pipe_peaks(device=None, stream=None):
     if rc:
         raise GivensBNError(rc)
     return float(f32.value), float(f64.value)
+
+
+def backward_batched_workspace_size(Xs, precision: int = 0, q: int = 0) -> int:
+    B, ns, ms = _batch_arrays(Xs)
+    o = _opts(precision, q)
+    b = ctypes.c_size_t(0)
+    rc = load().givensbn_backward_batched_workspace_size(ctypes.cast(ns, ctypes.c_void_p),
+                                                         ctypes.cast(ms, ctypes.c_void_p), B,
+                                                         ctypes.byref(o), ctypes.byref(b))
+    if rc:
+        raise GivensBNError(rc)
+    return int(b.value)
+
+
+def score_all_families_backward_batched(Xs, ws, *, precision: int = 0, q: int = 0,
+                                        center: bool = True, workspace=None, stream=None,
+                                        grads=None):
+    """Gradients of sum_f w_f * score_f for every dataset of a batch (one list of n x m float64
+    tensors); ws: one weight tensor per dataset, or one tensor shared by all (same m)."""
+    if not Xs:
+        raise ValueError("empty batch")
+    dev = Xs[0].device
+    for X in Xs:
+        if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float64
+                and X.dim() == 2 and X.is_contiguous() and X.device == dev):
+            raise TypeError("every X must be a contiguous 2-D float64 CUDA tensor on one device")
+    wdt = torch.float64 if precision else torch.float32
+    if isinstance(ws, torch.Tensor):
+        ws = [ws] * len(Xs)
+    ws = [w.to(device=dev, dtype=wdt).contiguous() for w in ws]
+    for X, w in zip(Xs, ws):
+        m = int(X.shape[1])
+        if w.numel() != m << (m - 1):
+            raise ValueError("each weight tensor must hold m * 2^(m-1) entries")
+    if grads is None:
+        grads = [torch.empty_like(X) for X in Xs]
+    B, ns, ms = _batch_arrays(Xs)
+    if workspace is None:
+        workspace = torch.empty(backward_batched_workspace_size(Xs, precision, q),
+                                dtype=torch.uint8, device=dev)
+    xp = (ctypes.c_void_p * B)(*[X.data_ptr() for X in Xs])
+    wp = (ctypes.c_void_p * B)(*[w.data_ptr() for w in ws])
+    gp = (ctypes.c_void_p * B)(*[g.data_ptr() for g in grads])
+    o = _opts(precision, q, center, False, _stream_handle(stream, dev), workspace)
+    rc = load().score_all_families_backward_batched(ctypes.cast(xp, ctypes.c_void_p),
+                                                    ctypes.cast(ns, ctypes.c_void_p),
+                                                    ctypes.cast(ms, ctypes.c_void_p), B,
+                                                    ctypes.cast(wp, ctypes.c_void_p),
+                                                    ctypes.cast(gp, ctypes.c_void_p),
+                                                    ctypes.byref(o))
+    if rc:
+        raise GivensBNError(rc)
+    return grads

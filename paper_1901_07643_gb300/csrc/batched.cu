@@ -249,3 +249,148 @@ extern "C" int score_all_families_batched(const double* const* Xs, const int64_t
     return launch_walk_batched(v, L.total_cta, L.Q, precision, opts->debug_coverage != 0,
                                L.n_cwarps, stream);
 }
+
+// ---------------------------------------------------------------- the adjoint of a batch
+// score_all_families_backward_batched: the R0 stage of every dataset as in a
+// scoring batch (the same kernels, so each R0 is bit-identical to a single
+// call's), then one launch of the adjoint walk over all datasets' sub-walks
+// (warp w of the launch belongs to the dataset whose warp range holds it),
+// one reduction launch and one gradient launch over (block, dataset).
+
+namespace {
+
+struct BwdBatchLayout {
+    BatchLayout L;
+    std::vector<int> Qb;
+    std::vector<int64_t> n_sub, warps;
+    std::vector<size_t> off_partials, off_gsym, off_muv;
+    size_t off_args = 0, off_prefix = 0, total = 0;
+    int64_t total_warps = 0;
+};
+
+int plan_bwd_batch(const int64_t* ns, const int32_t* ms, int32_t B, const givensbn_opts* opts,
+                   BwdBatchLayout* K) {
+    givensbn_opts o;
+    givensbn_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.shard_count > 1) return GBN_ERR_OPTS;
+    const int qreq = o.q;
+    o.q = 0;
+    o.consumer_warps = 0;
+    o.tune_cache = nullptr;
+    o.debug_coverage = 0;
+    int rc = plan_batch(ns, ms, B, &o, &K->L);
+    if (rc) return rc;
+    K->Qb.resize(B);
+    K->n_sub.resize(B);
+    K->warps.resize(B);
+    K->off_partials.resize(B);
+    K->off_gsym.resize(B);
+    K->off_muv.resize(B);
+    size_t off = K->L.total;
+    K->total_warps = 0;
+    for (int b = 0; b < B; ++b) {
+        if ((rc = bwd_subwalk_plan(ms[b], qreq, &K->Qb[b], &K->n_sub[b], &K->warps[b]))) return rc;
+        const size_t m = (size_t)ms[b];
+        K->off_partials[b] = off;
+        off = up256(off + sizeof(double) * (size_t)K->warps[b] * m * m);
+        K->off_gsym[b] = off;
+        off = up256(off + sizeof(double) * m * m);
+        K->off_muv[b] = off;
+        off = up256(off + sizeof(double) * 32);
+        K->total_warps += K->warps[b];
+    }
+    K->off_args = off;
+    off = up256(off + sizeof(BwdArgs) * B);
+    K->off_prefix = off;
+    off = up256(off + sizeof(int64_t) * (B + 1));
+    K->total = off;
+    return GBN_OK;
+}
+
+}  // namespace
+
+extern "C" int givensbn_backward_batched_workspace_size(const int64_t* ns, const int32_t* ms,
+                                                        int32_t B, const givensbn_opts* opts,
+                                                        size_t* bytes) {
+    if (!bytes) return GBN_ERR_NULL;
+    BwdBatchLayout K;
+    const int rc = plan_bwd_batch(ns, ms, B, opts, &K);
+    if (rc) return rc;
+    *bytes = K.total;
+    return GBN_OK;
+}
+
+extern "C" int score_all_families_backward_batched(const double* const* Xs, const int64_t* ns,
+                                                   const int32_t* ms, int32_t B,
+                                                   const void* const* weights,
+                                                   double* const* grads,
+                                                   const givensbn_opts* opts) {
+    if (!opts || !Xs || !weights || !grads) return GBN_ERR_NULL;
+    BwdBatchLayout K;
+    int rc = plan_bwd_batch(ns, ms, B, opts, &K);
+    if (rc) return rc;
+    const BatchLayout& L = K.L;
+    if (!opts->workspace || opts->workspace_bytes < K.total) return GBN_ERR_WORKSPACE;
+    if ((uintptr_t)opts->workspace & 255u) return GBN_ERR_ALIGN;
+    const int precision = opts->precision;
+    char* base = static_cast<char*>(opts->workspace);
+    cudaStream_t stream = static_cast<cudaStream_t>(opts->stream);
+    std::vector<const double*> X(B);
+    std::vector<char*> ws(B);
+    std::vector<void*> outp(B, nullptr);
+    for (int b = 0; b < B; ++b) {
+        if (!Xs[b] || !weights[b] || !grads[b]) return GBN_ERR_NULL;
+        if (((uintptr_t)Xs[b] & 7u) || ((uintptr_t)weights[b] & 15u) || ((uintptr_t)grads[b] & 7u))
+            return GBN_ERR_ALIGN;
+        X[b] = Xs[b];
+        ws[b] = base + L.ws_off[b];
+    }
+    // the scoring batch's device table (prefixes, plans, pointers) ...
+    std::vector<unsigned char> host(L.table_bytes, 0);
+    int64_t* cta_prefix = reinterpret_cast<int64_t*>(host.data() + L.off_cta_prefix);
+    int64_t* panel_prefix = reinterpret_cast<int64_t*>(host.data() + L.off_panel_prefix);
+    int32_t* dataset_of = reinterpret_cast<int32_t*>(host.data() + L.off_dataset_of);
+    cta_prefix[0] = panel_prefix[0] = 0;
+    for (int i = 0; i < B; ++i) {
+        const int b = L.launch_order[i];
+        dataset_of[i] = b;
+        cta_prefix[i + 1] = cta_prefix[i] + L.plans[b].n_cta;
+        panel_prefix[i + 1] = panel_prefix[i] + L.plans[b].panels;
+    }
+    memcpy(host.data() + L.off_plans, L.plans.data(), sizeof(Plan) * B);
+    memcpy(host.data() + L.off_X, X.data(), sizeof(void*) * B);
+    memcpy(host.data() + L.off_ws, ws.data(), sizeof(void*) * B);
+    memcpy(host.data() + L.off_out, outp.data(), sizeof(void*) * B);
+    if ((rc = upload(host, base, stream))) return rc;
+    // ... and the adjoint's: per-dataset arguments and the prefix of warps
+    std::vector<unsigned char> tail(K.total - K.off_args, 0);
+    BwdArgs* args = reinterpret_cast<BwdArgs*>(tail.data());
+    int64_t* warp_prefix = reinterpret_cast<int64_t*>(tail.data() + (K.off_prefix - K.off_args));
+    warp_prefix[0] = 0;
+    for (int b = 0; b < B; ++b) {
+        args[b] = bwd_args(L.plans[b], ws[b], X[b], weights[b], grads[b], K.Qb[b], K.n_sub[b],
+                           K.warps[b], reinterpret_cast<double*>(base + K.off_partials[b]),
+                           reinterpret_cast<double*>(base + K.off_gsym[b]),
+                           reinterpret_cast<double*>(base + K.off_muv[b]));
+        warp_prefix[b + 1] = warp_prefix[b] + K.warps[b];
+    }
+    if ((rc = upload(tail, base + K.off_args, stream))) return rc;
+    BatchView v;
+    v.B = B;
+    v.cta_prefix = reinterpret_cast<const int64_t*>(base + L.off_cta_prefix);
+    v.panel_prefix = reinterpret_cast<const int64_t*>(base + L.off_panel_prefix);
+    v.dataset_of = reinterpret_cast<const int32_t*>(base + L.off_dataset_of);
+    v.plans = reinterpret_cast<const Plan*>(base + L.off_plans);
+    v.X = reinterpret_cast<const double* const*>(base + L.off_X);
+    v.ws = reinterpret_cast<char* const*>(base + L.off_ws);
+    v.out = reinterpret_cast<void* const*>(base + L.off_out);
+    v.walk_args = nullptr;
+    v.pairs = 0;
+    int max_m = 1;
+    for (int b = 0; b < B; ++b) max_m = std::max(max_m, L.plans[b].m);
+    if ((rc = launch_r0_batched(v, L.total_panels, max_m, stream))) return rc;
+    return launch_bwd_batched(reinterpret_cast<const BwdArgs*>(base + K.off_args),
+                              reinterpret_cast<const int64_t*>(base + K.off_prefix), B,
+                              K.total_warps, precision, stream);
+}

@@ -203,6 +203,32 @@ __device__ __forceinline__ int batch_locate(const BatchView& v, const int64_t* p
 }
 
 int launch_r0_batched(const BatchView& v, int64_t total_panels, int max_m, cudaStream_t stream);
+
+// The adjoint walk of one dataset (backward.cu): its R0, weights, per-warp
+// FP64 partial sums of Gbar and the outputs.
+struct BwdArgs {
+    const double* R0;      // m x m, plan column order
+    const void* w;         // weights, table layout (float or double)
+    double* partials;      // [warps][m*m], one slot per warp of this dataset
+    int* status;
+    unsigned long long* chk;
+    int m, k, Q;
+    int64_t n_sub;         // 2^k sub-walks
+    int64_t warps;         // warps given to this dataset
+    double n;              // samples
+    int order[32];         // plan order: position -> variable of R0's columns
+    const double* X;       // the data (n x m), for grad_X = Xc (Gbar + Gbar^T)
+    int64_t rows;
+    const double* mu_plan; // column means, plan order
+    double* gsym;          // m x m: Gbar + Gbar^T
+    double* mu_var;        // the means by variable
+    double* grad;          // n x m output
+};
+int bwd_subwalk_plan(int m, int q_requested, int* Qb, int64_t* n_sub, int64_t* warps);
+BwdArgs bwd_args(const Plan& p, char* ws, const double* X, const void* w, double* grad, int Qb,
+                 int64_t n_sub, int64_t warps, double* partials, double* gsym, double* mu_var);
+int launch_bwd_batched(const BwdArgs* args, const int64_t* warp_prefix, int B, int64_t total_warps,
+                       int precision, cudaStream_t stream);
 int launch_roots_batched(const BatchView& v, int64_t total_cta, int Q, int max_w,
                          size_t max_stride, int precision, cudaStream_t stream);
 int launch_walk_batched(const BatchView& v, int64_t total_cta, int Q, int precision, bool coverage,
