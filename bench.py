@@ -233,6 +233,14 @@ def _cpu_baseline(X, n, m, seconds, gathered):  # noqa: C901
     for name, got in gathered.items():
         if name == "families":
             continue
+        if name == "bge":  # BGe scores against the BGe oracle on a prefix of the sample
+            from oracle import bge
+            cb, kb = gathered["families"]
+            ref_b = bge.scores_sampled(X, cb[:len(got)], kb[:len(got)])
+            scaled = np.abs(np.asarray(got, np.float64) - ref_b) / np.maximum(np.abs(ref_b), n)
+            errors[name] = {"max_scaled": float(scaled.max()), "count": int(len(ref_b)),
+                            "tolerance": 1e-4}
+            continue
         got = np.asarray(got[:len(ref)], np.float64)
         d = got - ref
         scaled = np.abs(d) / np.maximum(np.abs(ref), n)
@@ -458,6 +466,35 @@ def _extras(dev, flush, args):
     return out
 
 
+def _bge_leg(Xd, w, flush, slots_t, gathered):
+    """The BGe score of every family (score="bge": a factor of the posterior matrix, the
+    unchanged walk, the log-determinant recursion and an in-place pass over the table),
+    timed with CUDA events like the RSS-score call; its sampled values join the errors."""
+    import torch
+    from paper_1901_07643_gb300 import binding
+    dev = Xd.device
+    fam = w.m << (w.m - 1)
+    out = torch.empty(fam, dtype=torch.float32, device=dev)
+    ws = torch.empty(binding.workspace_size(w.n, w.m, score="bge"), dtype=torch.uint8,
+                     device=dev)
+    binding.score_all_families(Xd, out, workspace=ws, score="bge")  # warm-up and status check
+    ms = []
+    for _ in range(3):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        binding.score_all_families(Xd, out, workspace=ws, score="bge", check=False)
+        e[1].record()
+        torch.cuda.synchronize()
+        ms.append(e[0].elapsed_time(e[1]))
+    if slots_t is not None:
+        gathered["bge"] = out[slots_t[:4096]].double().cpu().numpy()
+    t = statistics.median(ms)
+    del out, ws
+    return {"workload": f"{w.name}, BGe score (alpha_mu 1, alpha_w m + 2)", "ms": t,
+            "value": fam / (t / 1e3), "unit": UNIT}
+
+
 def _search_leg(table, m, flush, args):
     """Exact structure search (best parents + subset dynamic programme) over the FP32 table
     just scored, timed with CUDA events; the best-parent transform's algorithmic HBM bytes
@@ -568,8 +605,9 @@ def run_ours(args):
     peaks = None
     try:  # measured FMA throughput: the FP64 walk's compute roofline
         f32, f64 = binding.pipe_peaks(local)
-        peaks = {"fp32_tflops": f32, "fp64_tflops": f64,
-                 "how": "independent FMA chains on every SM, best of 3 launches (CUDA events)"}
+        peaks = {"fp32_tflops": f32, "fp64_tflops": f64, "fp64_mma_tflops": binding.dmma_peak(local),
+                 "how": "independent FMA (or mma.sync m8n8k4 f64) chains on every SM, "
+                        "best of 3 launches (CUDA events)"}
     except Exception as e:  # noqa: BLE001 - reported, not fatal
         peaks = {"error": str(e)}
 
@@ -598,6 +636,9 @@ def run_ours(args):
         gathered["fp32"] = out32[slots_t].double().cpu().numpy()
     search_leg = None if args.skip_extras else _search_leg(out32, w.m, flush, args)
     del out32, ws32
+    torch.cuda.empty_cache()
+    bge_leg = None if args.skip_extras else _bge_leg(
+        Xd, w, flush, slots_t if want_errors else None, gathered)
     torch.cuda.empty_cache()
 
     fp64 = None
@@ -668,6 +709,8 @@ def run_ours(args):
     line.update(extras)
     if search_leg:
         line["structure_search"] = search_leg
+    if bge_leg:
+        line["bge"] = bge_leg
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -96,7 +96,8 @@ typedef struct givensbn_opts {
     int32_t max_parents;    /* bounded in-degree K: only families with |S| <= K are written (the
                                other slots of the table are left untouched); -1 = no bound
                                (default) */
-    int32_t score;          /* GBN_SCORE_BIC (default), GBN_SCORE_AIC or GBN_SCORE_PENALTY */
+    int32_t score;          /* GBN_SCORE_BIC (default), GBN_SCORE_AIC, GBN_SCORE_PENALTY or
+                               GBN_SCORE_BGE */
     double penalty;         /* GBN_SCORE_PENALTY: score = n ln(RSS/n) + penalty * |S| */
     int32_t shard_index;    /* score only shard shard_index of shard_count shards of the table */
     int32_t shard_count;    /* (see givensbn_shard_range); 0 or 1 = the whole table (default) */
@@ -105,12 +106,24 @@ typedef struct givensbn_opts {
     const char* tune_cache; /* host path of an autotuner cache file (givensbn_autotune), or NULL.
                                With q == 0 and consumer_warps == 0 the plan takes the cached
                                choice for this device and size class, else the automatic one */
+    double bge_alpha_mu;    /* GBN_SCORE_BGE: prior precision scale of the mean, > 0; 0 = 1 */
+    double bge_alpha_w;     /* GBN_SCORE_BGE: prior Wishart degrees of freedom, > m + 1;
+                               0 = m + 2 */
 } givensbn_opts;
 
 /* Score of a family from its residual sum of squares (opts->score). */
 #define GBN_SCORE_BIC 0     /* n ln(RSS/n) + |S| ln n */
 #define GBN_SCORE_AIC 1     /* n ln(RSS/n) + 2 |S| */
 #define GBN_SCORE_PENALTY 2 /* n ln(RSS/n) + opts->penalty * |S| */
+/* BGe: the log marginal likelihood ratio ln p(d_{S u c}) - ln p(d_S) under the normal-Wishart
+ * prior (Geiger and Heckerman 2002, corrected by Kuipers, Moffa and Heckerman 2014) with prior
+ * mean the sample mean and T0 = t I, t = alpha_mu (alpha_w - m - 1) / (alpha_mu + 1).  The walk
+ * runs over a factor of the posterior matrix t I + S_n (S_n the centred scatter matrix), so its
+ * residuals are the Schur complements rho(c | S); a pass then forms ln det of every parent
+ * block by the recursion L[S] = L[S - h] + ln rho(h | S - h) (h the highest variable of S) and
+ * writes K(|S|) - ((n + alpha_w - m + |S| + 1) / 2) ln rho(c | S) - L[S] / 2.  Single-dataset
+ * calls without shards only; the workspace grows by 2^m table elements. */
+#define GBN_SCORE_BGE 3
 
 /* Default options: FP32, centring on, automatic q, no workspace, fixup_tau 1e-6, BIC score, no
  * in-degree bound, the whole table, the default watchdog, no tuning cache. */
@@ -212,7 +225,7 @@ int givensbn_batched_workspace_size(const int64_t* ns, const int32_t* ms, int32_
  *           FP32 walk state) or double (precision 1), 16-byte aligned
  *   grad_X  device, n x m FP64 row-major, written (not accumulated)
  *   opts    host; workspace >= givensbn_backward_workspace_size(); opts->q is
- *           the sub-walk size of the backward walk (0 = automatic, m - 10)
+ *           the sub-walk size of the backward walk (0 = automatic, m - 9)
  * Families with RSS == 0 contribute nothing (their score is -inf); a singular
  * sub-walk factor sets GBN_STATUS_RANK_DEFICIENT and is skipped.
  * Deterministic: sums are formed in a fixed order.  Returns 0 or GBN_ERR_*.
@@ -234,7 +247,7 @@ int givensbn_backward_workspace_size(int64_t n, int32_t m, const givensbn_opts* 
  *   weights     host array of B device pointers, weights of dataset b in its table layout
  *               (m_b 2^(m_b-1) entries; float for precision 0, double for 1), 16-byte aligned
  *   grads       host array of B device pointers, n_b x m_b FP64 outputs
- *   opts        host; opts->q is the backward sub-walk size (0 = m - 10 per dataset);
+ *   opts        host; opts->q is the backward sub-walk size (0 = m - 9 per dataset);
  *               workspace >= givensbn_backward_batched_workspace_size()
  * Returns 0 or GBN_ERR_*; per-dataset status words are not read by givensbn_status.
  */
@@ -378,6 +391,16 @@ int givensbn_best_parents(const float* scores, int32_t m, float* best, uint32_t*
  * Returns 0 or GBN_ERR_*.
  */
 int givensbn_pipe_peaks(void* scratch, void* stream, double* fp32_tflops, double* fp64_tflops);
+/*
+ * Measured FP64 tensor-core throughput of the current device (a measurement helper, not part
+ * of the paper's method): independent chains of mma.sync m8n8k4 f64 on every SM, 512 flops
+ * per warp instruction, TFLOP/s, best of three timed launches.  It is the rate an FP64 Gram
+ * on the matrix units could reach, beside the FMA rate of givensbn_pipe_peaks.
+ *   scratch  device, 8 bytes, 8-byte aligned (never written for these inputs)
+ *   stream   cudaStream_t (synchronised)
+ * Returns 0 or GBN_ERR_*.
+ */
+int givensbn_dmma_peak(void* scratch, void* stream, double* tflops);
 int givensbn_structure_search_workspace_size(int32_t m, size_t* bytes);
 int givensbn_structure_search(const float* scores, int32_t m, uint32_t* parents, int32_t* order,
                               double* total, const givensbn_opts* opts);

@@ -49,17 +49,20 @@ def ln_mvgamma(p: int, x: float) -> float:
                                                        for j in range(1, p + 1))
 
 
-def ln_marginal(X, Y, alpha_mu: float = 1.0, alpha_w: float | None = None) -> float:
-    """ln p(d_Y) for the variable set Y (a list of column indices) of data X (n x m)."""
+def _posterior(X, alpha_mu, alpha_w):
+    """(n, m, alpha_mu, alpha_w, t, R) with R = t I + S_n (nu = xbar)."""
     X = np.asarray(X, dtype=np.float64)
     n, m = X.shape
     am, aw, t = prior(m, alpha_mu, alpha_w)
-    Y = list(Y)
+    Xc = X - X.mean(axis=0)
+    return n, m, am, aw, t, t * np.eye(m) + Xc.T @ Xc
+
+
+def _ln_p(R, Y, n, m, am, aw, t) -> float:
+    """ln p(d_Y) from the posterior matrix R (the formula of the module docstring)."""
     k = len(Y)
     if k == 0:
         return 0.0
-    Xc = X - X.mean(axis=0)
-    R = t * np.eye(m) + Xc.T @ Xc
     sign, logdet_r = np.linalg.slogdet(R[np.ix_(Y, Y)])
     if sign <= 0:
         raise ValueError("R_YY is not positive definite")
@@ -68,18 +71,33 @@ def ln_marginal(X, Y, alpha_mu: float = 1.0, alpha_w: float | None = None) -> fl
             + (aw - m + k) / 2.0 * k * math.log(t) - (n + aw - m + k) / 2.0 * logdet_r)
 
 
+def ln_marginal(X, Y, alpha_mu: float = 1.0, alpha_w: float | None = None) -> float:
+    """ln p(d_Y) for the variable set Y (a list of column indices) of data X (n x m)."""
+    n, m, am, aw, t, R = _posterior(X, alpha_mu, alpha_w)
+    return _ln_p(R, list(Y), n, m, am, aw, t)
+
+
 def scores(X, alpha_mu: float = 1.0, alpha_w: float | None = None) -> np.ndarray:
     """Every family's BGe local score in table layout: slot c * 2^(m-1) + the parent mask
     with bit c removed (the layout of the library's score table)."""
-    X = np.asarray(X, dtype=np.float64)
-    n, m = X.shape
+    n, m, am, aw, t, R = _posterior(X, alpha_mu, alpha_w)
     lnp = np.empty(1 << m)
     for S in range(1 << m):
-        lnp[S] = ln_marginal(X, [v for v in range(m) if (S >> v) & 1], alpha_mu, alpha_w)
+        lnp[S] = _ln_p(R, [v for v in range(m) if (S >> v) & 1], n, m, am, aw, t)
     half = 1 << (m - 1)
     out = np.empty(m * half)
     for c in range(m):
         for cm in range(half):
             S = (cm & ((1 << c) - 1)) | ((cm >> c) << (c + 1))
             out[c * half + cm] = lnp[S | (1 << c)] - lnp[S]
+    return out
+
+
+def scores_sampled(X, child, mask, alpha_mu: float = 1.0, alpha_w: float | None = None):
+    """BGe scores of listed families (child[i], parent bitmask mask[i]) of data X."""
+    n, m, am, aw, t, R = _posterior(X, alpha_mu, alpha_w)
+    out = np.empty(len(child))
+    for i, (c, S) in enumerate(zip(child, mask)):
+        par = [v for v in range(m) if (int(S) >> v) & 1]
+        out[i] = _ln_p(R, sorted(par + [int(c)]), n, m, am, aw, t) - _ln_p(R, par, n, m, am, aw, t)
     return out

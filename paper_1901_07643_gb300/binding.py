@@ -24,8 +24,8 @@ GBN_STATUS_WATCHDOG = 2
 GBN_STATUS_FIXUP_OVERFLOW = 4
 GBN_STATUS_BAD_FAMILY = 8
 
-SCORE_BIC, SCORE_AIC, SCORE_PENALTY = 0, 1, 2
-_SCORES = {"bic": SCORE_BIC, "aic": SCORE_AIC, "penalty": SCORE_PENALTY}
+SCORE_BIC, SCORE_AIC, SCORE_PENALTY, SCORE_BGE = 0, 1, 2, 3
+_SCORES = {"bic": SCORE_BIC, "aic": SCORE_AIC, "penalty": SCORE_PENALTY, "bge": SCORE_BGE}
 
 
 def _check_status(st: int) -> None:
@@ -59,6 +59,8 @@ class Opts(ctypes.Structure):
         ("consumer_warps", ctypes.c_int32),
         ("reserved0", ctypes.c_int32),
         ("tune_cache", ctypes.c_char_p),
+        ("bge_alpha_mu", ctypes.c_double),
+        ("bge_alpha_w", ctypes.c_double),
     ]
 
 
@@ -109,6 +111,7 @@ def load():
             lib.givensbn_family_coefficients.argtypes = [P, i64, i32, P, P, i64, P, P, OP]
             lib.givensbn_best_parents.argtypes = [P, i32, P, P, OP]
             lib.givensbn_pipe_peaks.argtypes = [P, P, DP, DP]
+            lib.givensbn_dmma_peak.argtypes = [P, P, DP]
             lib.score_all_families_backward_batched.argtypes = [P, P, P, i32, P, P, OP]
             lib.givensbn_backward_batched_workspace_size.argtypes = [P, P, i32, OP, SZP]
             lib.givensbn_structure_search_workspace_size.argtypes = [i32, SZP]
@@ -134,7 +137,7 @@ def auto_q(m: int, precision: int = 0) -> int:
 def _opts(precision=0, q=0, center=True, debug_coverage=False, stream=None,
           workspace=None, stage_events=None, fixup_tau=None, *, score="bic", penalty=0.0,
           max_parents=None, shard=None, consumer_warps=0, watchdog_ns=0,
-          tune_cache=None) -> Opts:
+          tune_cache=None, bge_alpha_mu=0.0, bge_alpha_w=0.0) -> Opts:
     o = Opts()
     load().givensbn_default_opts(ctypes.byref(o))
     if fixup_tau is not None:
@@ -143,6 +146,8 @@ def _opts(precision=0, q=0, center=True, debug_coverage=False, stream=None,
         raise ValueError(f"score must be one of {sorted(_SCORES)}")
     o.score = _SCORES[score]
     o.penalty = float(penalty)
+    o.bge_alpha_mu = float(bge_alpha_mu)
+    o.bge_alpha_w = float(bge_alpha_w)
     o.max_parents = -1 if max_parents is None else int(max_parents)
     if shard is not None:
         o.shard_index, o.shard_count = int(shard[0]), int(shard[1])
@@ -169,7 +174,7 @@ def _opts(precision=0, q=0, center=True, debug_coverage=False, stream=None,
 
 # keyword options of the scoring calls that shape the plan (see givensbn_opts)
 _PLAN_KEYS = ("score", "penalty", "max_parents", "shard", "consumer_warps", "watchdog_ns",
-              "tune_cache")
+              "tune_cache", "bge_alpha_mu", "bge_alpha_w")
 
 
 def workspace_size(n: int, m: int, precision: int = 0, q: int = 0, fixup_tau=None,
@@ -231,10 +236,11 @@ def score_all_families(X: torch.Tensor, out: torch.Tensor | None = None, *, prec
     tensor: the kernels then write the table straight into host memory.  check=True synchronises
     and warns if the data were rank deficient.  stage_events: four
     torch.cuda.Event(enable_timing=True) recorded at the stage boundaries.
-    Further keyword options (givensbn_opts): score ("bic", "aic", "penalty") and
-    penalty, max_parents (in-degree bound; slots of larger families are left as
-    they are in `out`), shard = (index, count), consumer_warps, watchdog_ns,
-    tune_cache (path of the autotuner's cache file).
+    Further keyword options (givensbn_opts): score ("bic", "aic", "penalty", "bge") with
+    penalty or bge_alpha_mu / bge_alpha_w (0 = the defaults 1 and m + 2), max_parents
+    (in-degree bound; slots of larger families are left as they are in `out`),
+    shard = (index, count), consumer_warps, watchdog_ns, tune_cache (path of the
+    autotuner's cache file).
     """
     for key in plan:
         if key not in _PLAN_KEYS:
@@ -605,6 +611,18 @@ def pipe_peaks(device=None, stream=None):
     if rc:
         raise GivensBNError(rc)
     return float(f32.value), float(f64.value)
+
+
+def dmma_peak(device=None, stream=None):
+    """Measured FP64 tensor-core (mma.sync m8n8k4 f64) throughput, TFLOP/s (givensbn_dmma_peak)."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    scratch = torch.empty(1, dtype=torch.float64, device=dev)
+    t = ctypes.c_double(0)
+    rc = load().givensbn_dmma_peak(ctypes.c_void_p(scratch.data_ptr()), _stream_handle(stream, dev),
+                                   ctypes.byref(t))
+    if rc:
+        raise GivensBNError(rc)
+    return float(t.value)
 
 
 def backward_batched_workspace_size(Xs, precision: int = 0, q: int = 0) -> int:

@@ -72,12 +72,21 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     if (Q < kMinQ || Q > max_q(precision) || Q > m) return GBN_ERR_Q;
     const int score = opts ? opts->score : GBN_SCORE_BIC;
     double lam;
+    double bge_am = 0.0, bge_aw = 0.0;
     switch (score) {
         case GBN_SCORE_BIC: lam = log((double)n); break;
         case GBN_SCORE_AIC: lam = 2.0; break;
         case GBN_SCORE_PENALTY:
             lam = opts->penalty;
             if (!(lam == lam) || lam > 1e300 || lam < -1e300) return GBN_ERR_OPTS;
+            break;
+        case GBN_SCORE_BGE:  // the walk stores n ln(rho / n); the BGe pass does the rest
+            lam = 0.0;
+            bge_am = opts->bge_alpha_mu == 0.0 ? 1.0 : opts->bge_alpha_mu;
+            bge_aw = opts->bge_alpha_w == 0.0 ? (double)m + 2.0 : opts->bge_alpha_w;
+            if (!(bge_am > 0.0 && bge_am < 1e300 && bge_aw > (double)m + 1.0 && bge_aw < 1e300))
+                return GBN_ERR_OPTS;
+            if (opts->debug_coverage) return GBN_ERR_OPTS;
             break;
         default: return GBN_ERR_OPTS;
     }
@@ -86,6 +95,7 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     if (shard_count < 0 || shard_index < 0 || (shard_count <= 1 ? shard_index != 0
                                                                   : shard_index >= shard_count))
         return GBN_ERR_OPTS;
+    if (score == GBN_SCORE_BGE && shard_count > 1) return GBN_ERR_OPTS;  // needs every family
     const long long wd = opts ? (long long)opts->watchdog_ns : 0;
     if (wd < 0) return GBN_ERR_OPTS;
     *p = Plan();
@@ -102,6 +112,12 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     p->cta_begin = cb;
     p->n_cta = ce - cb;
     p->lam = lam;
+    if (score == GBN_SCORE_BGE) {
+        p->bge = 1;
+        p->bge_alpha_mu = bge_am;
+        p->bge_alpha_w = bge_aw;
+        p->bge_t = bge_am * (bge_aw - m - 1.0) / (bge_am + 1.0);
+    }
     const int mp = opts ? opts->max_parents : -1;
     p->kmax = (mp < 0 || mp > m - 1) ? m - 1 : mp;
     p->watchdog_ns = wd > 0 ? wd : kWatchdogNs;
@@ -147,6 +163,10 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
         p->off_fix = off;
         off = align_up(off + 256 + sizeof(long long) * (size_t)kFixCap, 256);
     }
+    if (p->bge) {
+        p->off_bge = off;
+        off = align_up(off + es * ((size_t)1 << m), 256);
+    }
     p->total_bytes = off;
     return GBN_OK;
 }
@@ -186,6 +206,7 @@ int run_pipeline(const Plan& p, const double* X, char* ws, void* out, cudaStream
     cudaEvent_t* ev = static_cast<cudaEvent_t*>(stage_events);
     if (ev && cudaEventRecord(ev[0], stream) != cudaSuccess) return GBN_ERR_CUDA;
     int rc = launch_r0(p, X, ws, stream);
+    if (rc == GBN_OK && p.bge) rc = launch_bge_prior(p, ws, stream);
     if (rc == GBN_OK && p.fix_cap) rc = launch_fix_flags(p, ws, stream);
     if ((rc = checked_stage("r0", rc, p, ws, stream))) return rc;
     if (ev && cudaEventRecord(ev[1], stream) != cudaSuccess) return GBN_ERR_CUDA;
@@ -198,6 +219,10 @@ int run_pipeline(const Plan& p, const double* X, char* ws, void* out, cudaStream
     if (p.fix_cap) {
         rc = launch_fixup(p, ws, out, stream);
         if ((rc = checked_stage("fixup", rc, p, ws, stream))) return rc;
+    }
+    if (p.bge) {
+        rc = launch_bge_finalize(p, ws, out, stream);
+        if ((rc = checked_stage("bge", rc, p, ws, stream))) return rc;
     }
     return GBN_OK;
 }

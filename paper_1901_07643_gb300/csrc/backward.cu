@@ -34,36 +34,43 @@ namespace {
 
 constexpr int kBwdWarps = 2;  // warps per block
 constexpr int64_t kBwdMaxWarps = 4096;  // warps given to one dataset
-constexpr int kLd = 33;       // row stride of R and A (one slot per lane; odd: conflict-free)
-constexpr int kLdW = 33;      // row stride of the tail sums
-constexpr int kLdY = 33;      // row stride of the FP64 transform scratch
+constexpr int kStepTab = 1024;  // swap positions kept per warp (every Q <= 10)
 
-// Per warp.  The tail sums and the children's alphas are needed during the
-// walk only, the FP64 transform scratch after it: they share storage.
-template <typename T>
+// Per warp; MW (16 or 32) is the widest factor the warp holds.  For MW = 16
+// the two half-warps hold the same columns and split the rows of the rank
+// update between them.  The tail sums and the children's list are needed
+// during the walk only, the FP64 transform scratch after it: they share
+// storage.
+template <typename T, int MW>
 struct BwdWarpSmem {
-    T R[32 * kLd];  // R[row * kLd + slot]
-    T A[32 * kLd];  // A[row * kLd + col] (symmetric, both triangles), R's row basis
+    static constexpr int LD = MW + 1;  // odd row stride: conflict-free column reads
+    T R[MW * LD];                      // R[row * LD + slot]
+    T A[MW * LD];                      // A[row * LD + col] (symmetric), R's row basis
     union {
         struct {
-            T Wt[33 * kLdW];  // Wt[r * kLdW + slot] = sum_{t >= r} R[t][slot]^2
-            T P[32];          // alpha of each child slot of the current prefix
+            T Wt[(MW + 1) * LD];  // Wt[r * LD + slot] = sum_{t >= r} R[t][slot]^2
+            T P[MW];              // alpha of the current prefix's children, by rank
+            int cl[MW];           // their slots, by rank
         };
-        double Y[32 * kLdY];  // R_T^{-1} A, then Gbar_sub (positions)
+        double Y[MW * LD];  // R_T^{-1} A, then Gbar_sub (positions)
     };
-    double dinv[32];  // 1 / R_T[p][p] by position
-    int var_at_pos[32];
-    int slot_at_pos[32];
+    double dinv[MW];  // 1 / R_T[p][p] by position
+    int var_at_pos[MW];
+    int slot_at_pos[MW];
+    unsigned char ups[kStepTab];  // Upsilon(Q): the swap position of every step
 };
+
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
 
 template <typename T>
 __device__ __forceinline__ void givens_cs(T a, T b, T& c, T& s, T& rho) {
     const T r2 = a * a + b * b;
     if (r2 > T(0)) {
-        const T r = sqrt(r2);
-        c = a / r;
-        s = b / r;
-        rho = r;
+        const T inv = rsqrt_t(r2);
+        c = a * inv;
+        s = b * inv;
+        rho = r2 * inv;
     } else {
         c = T(1);
         s = T(0);
@@ -71,106 +78,148 @@ __device__ __forceinline__ void givens_cs(T a, T b, T& c, T& s, T& rho) {
     }
 }
 
+// alpha = w n / RSS: the fast reciprocal-multiply in FP32 (2 ulp), IEEE in FP64
+__device__ __forceinline__ float fast_div(float x, float y) { return __fdividef(x, y); }
+__device__ __forceinline__ double fast_div(double x, double y) { return x / y; }
+
+__device__ __forceinline__ int swapped(int pos, int s) {
+    return pos == s ? s + 1 : (pos == s + 1 ? s : pos);
+}
+
 // GRC at position s: swap the columns at positions s and s+1, then restore
 // triangularity with one rotation of rows s, s+1.  with_A also conjugates A
 // (A -> G A G^T): lane j rotates its entries of rows s, s+1; by symmetry
 // they are also column j's entries of columns s, s+1, except in the 2 x 2
 // block, which lane s rotates on both sides; and the tail sums of row s+1.
-template <typename T>
-__device__ __forceinline__ void grc(BwdWarpSmem<T>& S, int m, int lane, int& mypos, int s,
-                                    bool with_A) {
-    if (mypos == s)
-        mypos = s + 1;
-    else if (mypos == s + 1)
-        mypos = s;
+// col = the lane's column slot; only the lead half-warp stores.
+template <typename T, int MW>
+__device__ __forceinline__ void grc(BwdWarpSmem<T, MW>& S, int m, int col, bool lead, int& mypos,
+                                    int s, bool with_A) {
+    constexpr int LD = MW + 1;
+    mypos = swapped(mypos, s);
     const unsigned at_s = __ballot_sync(0xffffffffu, mypos == s);
-    const int ls = __ffs(at_s) - 1;
-    const T a = S.R[s * kLd + ls], b = S.R[(s + 1) * kLd + ls];
+    const int ls = __ffs(at_s) - 1;  // a lead lane: the lowest set bit
+    const T a = S.R[s * LD + ls], b = S.R[(s + 1) * LD + ls];
     T c, sn, rho;
     givens_cs(a, b, c, sn, rho);
-    const T x = S.R[s * kLd + lane], y = S.R[(s + 1) * kLd + lane];
+    const T x = S.R[s * LD + col], y = S.R[(s + 1) * LD + col];
     T ax = T(0), ay = T(0);
     if (with_A) {
-        ax = S.A[s * kLd + lane];
-        ay = S.A[(s + 1) * kLd + lane];
+        ax = S.A[s * LD + col];
+        ay = S.A[(s + 1) * LD + col];
     }
     __syncwarp();
-    const T ry = (lane == ls) ? T(0) : c * y - sn * x;
-    S.R[s * kLd + lane] = (lane == ls) ? rho : c * x + sn * y;
-    S.R[(s + 1) * kLd + lane] = ry;
+    const T ry = (col == ls) ? T(0) : c * y - sn * x;
+    if (lead) {
+        S.R[s * LD + col] = (col == ls) ? rho : c * x + sn * y;
+        S.R[(s + 1) * LD + col] = ry;
+    }
     if (with_A) {
         const T nx = c * ax + sn * ay, ny = c * ay - sn * ax;  // rows of G A
         const T nxs = __shfl_sync(0xffffffffu, nx, s), nxs1 = __shfl_sync(0xffffffffu, nx, s + 1);
         const T nys = __shfl_sync(0xffffffffu, ny, s), nys1 = __shfl_sync(0xffffffffu, ny, s + 1);
-        if (lane < m && lane != s && lane != s + 1) {
-            S.A[s * kLd + lane] = nx;
-            S.A[(s + 1) * kLd + lane] = ny;
-            S.A[lane * kLd + s] = nx;
-            S.A[lane * kLd + s + 1] = ny;
+        if (lead && col < m && col != s && col != s + 1) {
+            S.A[s * LD + col] = nx;
+            S.A[(s + 1) * LD + col] = ny;
+            S.A[col * LD + s] = nx;
+            S.A[col * LD + s + 1] = ny;
         }
-        if (lane == s) {
-            S.A[s * kLd + s] = c * nxs + sn * nxs1;
-            S.A[s * kLd + s + 1] = c * nxs1 - sn * nxs;
-            S.A[(s + 1) * kLd + s] = c * nys + sn * nys1;
-            S.A[(s + 1) * kLd + s + 1] = c * nys1 - sn * nys;
+        if (lead && col == s) {
+            S.A[s * LD + s] = c * nxs + sn * nxs1;
+            S.A[s * LD + s + 1] = c * nxs1 - sn * nxs;
+            S.A[(s + 1) * LD + s] = c * nys + sn * nys1;
+            S.A[(s + 1) * LD + s + 1] = c * nys1 - sn * nys;
         }
         // the rotation keeps R[s][j]^2 + R[s+1][j]^2: only row s+1's tail sum changes
-        S.Wt[(s + 1) * kLdW + lane] = fma(ry, ry, S.Wt[(s + 2) * kLdW + lane]);
+        if (lead) S.Wt[(s + 1) * LD + col] = fma(ry, ry, S.Wt[(s + 2) * LD + col]);
     }
     __syncwarp();
+}
+
+// The weight w_f of this lane's family when the prefix has length a0 and the
+// lane's column sits at position pos (0 unless that column is a child).  Its
+// load is issued one step ahead of the family's rank update.
+template <typename T>
+__device__ __forceinline__ T family_weight(const BwdArgs& g, const T* __restrict__ w, int col,
+                                           int pos, int var, int a0) {
+    const int m = g.m;
+    const unsigned mask = __reduce_or_sync(0xffffffffu,
+                                           (col < m && pos < a0) ? (1u << var) : 0u);
+    if (!(col < m && pos >= a0)) return T(0);
+    const unsigned low = mask & ((1u << var) - 1u);
+    const unsigned high = (mask >> (var + 1)) << var;
+    const int64_t slot = ((int64_t)var << (m - 1)) + (int64_t)(low | high);
+    return GBN_IN(g.chk, 301, slot, (int64_t)m << (m - 1)) ? w[slot] : T(0);
 }
 
 // Families of the current ordering with prefix length a0: every column at a
 // position >= a0 is a child (its RSS the tail sum of its slot from row a0),
 // the parents are the columns at positions < a0.  Then
-// A[r][j] += sum_c alpha_c R[r][c] R[j][c] for rows r, j >= a0 (lane = j).
-template <typename T>
-__device__ __forceinline__ void emit(BwdWarpSmem<T>& S, const BwdArgs& g, const T* __restrict__ w,
-                                     int lane, int mypos, int myvar, int a0) {
+// A[r][j] += sum_c alpha_c R[r][c] R[j][c] for rows r, j >= a0 (j = col).
+template <typename T, int MW>
+__device__ __forceinline__ void emit(BwdWarpSmem<T, MW>& S, const BwdArgs& g, int col, int ph,
+                                     int mypos, int a0, T wf) {
+    constexpr int LD = MW + 1;
     const int m = g.m;
-    const unsigned mask = __reduce_or_sync(0xffffffffu,
-                                           (lane < m && mypos < a0) ? (1u << myvar) : 0u);
-    const bool child = lane < m && mypos >= a0;
+    const bool child = col < m && mypos >= a0;
     T alpha = T(0);
     if (child) {
-        const unsigned low = mask & ((1u << myvar) - 1u);
-        const unsigned high = (mask >> (myvar + 1)) << myvar;
-        const int64_t slot = ((int64_t)myvar << (m - 1)) + (int64_t)(low | high);
-        const T rss = S.Wt[a0 * kLdW + lane];
-        if (GBN_IN(g.chk, 301, slot, (int64_t)m << (m - 1))) {
-            const T wf = w[slot];
-            if (rss > T(0)) alpha = wf * (T)g.n / rss;
-        }
+        const T rss = S.Wt[a0 * LD + col];
+        if (rss > T(0)) alpha = fast_div(wf * (T)g.n, rss);
     }
-    S.P[lane] = alpha;
-    const unsigned cm = __ballot_sync(0xffffffffu, child && alpha != T(0));
+    const unsigned cm = __ballot_sync(0xffffffffu, child && alpha != T(0)) &
+                        (MW == 32 ? 0xffffffffu : ((1u << MW) - 1u));
+    // the children as a list (warp-uniform): each child lane puts its slot and alpha at
+    // its rank
+    if (ph == 0 && ((cm >> col) & 1u)) {
+        const int rank = __popc(cm & ((1u << col) - 1u));
+        S.cl[rank] = col;
+        S.P[rank] = alpha;
+    }
     __syncwarp();
     if (!cm) return;
-    // the children as a list (warp-uniform): slot c_i and t_i = alpha_i R[lane][c_i] in
-    // registers, so each (row, child) term is one broadcast load and one FMA
     const int nc = __popc(cm);
-    int cs[32];
-    T t[32];
-    unsigned rest = cm;
+    if constexpr (MW == 16) {
+        // children outer, this half's rows ph, ph + 2, ... in registers: per child one
+        // t_i = alpha_i R[col][c_i], then one broadcast load and one FMA per row
+        T acc[8];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        if (i < nc) {
-            const int c = __ffs(rest) - 1;
-            rest &= rest - 1;
-            cs[i] = c;
-            t[i] = S.P[c] * S.R[lane * kLd + c];
+        for (int j = 0; j < 8; ++j) acc[j] = T(0);
+        for (int i = 0; i < nc; ++i) {
+            const int c = S.cl[i];
+            const T ti = S.P[i] * S.R[col * LD + c];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] = fma(ti, S.R[(ph + 2 * j) * LD + c], acc[j]);
         }
-    }
-    if (lane >= a0 && lane < m) {
-        for (int r = a0; r < m; ++r) {
-            const T* Rr = S.R + r * kLd;
-            T acc0 = S.A[r * kLd + lane], acc1 = T(0);
+        if (col >= a0 && col < m) {
 #pragma unroll
-            for (int i = 0; i < 32; i += 2) {
-                if (i < nc) acc0 = fma(t[i], Rr[cs[i]], acc0);
-                if (i + 1 < nc) acc1 = fma(t[i + 1], Rr[cs[i + 1]], acc1);
+            for (int j = 0; j < 8; ++j) {
+                const int r = ph + 2 * j;
+                if (r >= a0 && r < m) S.A[r * LD + col] += acc[j];
             }
-            S.A[r * kLd + lane] = acc0 + acc1;
+        }
+    } else {  // MW = 32: rows outer, the children (slot c_i and t_i) in registers
+        int cs[MW];
+        T t[MW];
+#pragma unroll
+        for (int i = 0; i < MW; ++i) {
+            if (i < nc) {
+                const int c = S.cl[i];
+                cs[i] = c;
+                t[i] = S.P[i] * S.R[col * LD + c];
+            }
+        }
+        if (col >= a0 && col < m) {
+            for (int r = a0; r < m; ++r) {
+                const T* Rr = S.R + r * LD;
+                T acc0 = S.A[r * LD + col], acc1 = T(0);
+#pragma unroll
+                for (int i = 0; i < MW; i += 2) {
+                    if (i < nc) acc0 = fma(t[i], Rr[cs[i]], acc0);
+                    if (i + 1 < nc) acc1 = fma(t[i + 1], Rr[cs[i + 1]], acc1);
+                }
+                S.A[r * LD + col] = acc0 + acc1;
+            }
         }
     }
     __syncwarp();
@@ -178,32 +227,42 @@ __device__ __forceinline__ void emit(BwdWarpSmem<T>& S, const BwdArgs& g, const 
 
 // The sub-walks lw, lw + nw, ... of one dataset, by one warp; Gbar_sub of
 // each is added to this warp's FP64 partial sum (partials slot lw).
-template <typename T>
+template <typename T, int MW>
 __device__ __forceinline__ void bwd_subwalks(const BwdArgs& g, int64_t lw, int64_t nw,
-                                             BwdWarpSmem<T>& S) {
+                                             BwdWarpSmem<T, MW>& S) {
+    constexpr int LD = MW + 1;
+    constexpr int kPh = 32 / MW;
     const int lane = threadIdx.x & 31;
+    const int col = lane & (MW - 1);
+    const int ph = lane / MW;
+    const bool lead = ph == 0;
     const int m = g.m, k = g.k, Q = g.Q;
     const T* __restrict__ w = static_cast<const T*>(g.w);
     double* part = g.partials + lw * (int64_t)(m * m);
     for (int e = lane; e < m * m; e += 32) part[e] = 0.0;
     const int64_t nsteps = ((int64_t)1 << Q) - Q - 1;
     const unsigned hmask = k > 0 ? (unsigned)((1ull << k) - 1ull) : 0u;
+    const bool tab = nsteps <= kStepTab;  // the sequence once per warp, else step by step
+    if (tab)
+        for (int64_t t = lane; t < nsteps; t += 32) S.ups[t] = (unsigned char)upsilon_at(Q, t);
+    __syncwarp();
+    auto ups_at = [&](int64_t t) { return tab ? (int)S.ups[t] : upsilon_at(Q, t); };
 
     for (int64_t sub = lw; sub < g.n_sub; sub += nw) {
         const unsigned F = (unsigned)sub;  // bit v set: fixed variable v is in the front set
         const int d = __popc(F);
         // checkpoint: R0 in plan order, slot = plan position
-        for (int r = 0; r < 32; ++r) {
+        for (int r = ph; r < MW; r += kPh) {
             T v = T(0);
-            if (lane < m && r < m && GBN_IN(g.chk, 302, r * m + lane, m * m)) v = (T)g.R0[r * m + lane];
-            S.R[r * kLd + lane] = v;
-            S.A[r * kLd + lane] = T(0);
+            if (col < m && r < m && GBN_IN(g.chk, 302, r * m + col, m * m)) v = (T)g.R0[r * m + col];
+            S.R[r * LD + col] = v;
+            S.A[r * LD + col] = T(0);
         }
-        const int myvar = lane < m ? g.order[lane] : 0;
-        int mypos = lane;
+        const int myvar = col < m ? g.order[col] : 0;
+        int mypos = col;
         // target position in [F ascending, L = k..m-1, (H \ F) ascending]
-        int tpos = lane;
-        if (lane < m) {
+        int tpos = col;
+        if (col < m) {
             const unsigned below = (1u << myvar) - 1u;
             if (myvar >= k)
                 tpos = d + (myvar - k);
@@ -214,80 +273,98 @@ __device__ __forceinline__ void bwd_subwalks(const BwdArgs& g, int64_t lw, int64
         }
         __syncwarp();
         for (int p = 0; p < m; ++p) {  // sort by GRC steps; positions < p are final
-            const int owner = __ffs(__ballot_sync(0xffffffffu, lane < m && tpos == p)) - 1;
+            const int owner = __ffs(__ballot_sync(0xffffffffu, col < m && tpos == p)) - 1;
             const int q = __shfl_sync(0xffffffffu, mypos, owner);
-            for (int s = q - 1; s >= p; --s) grc(S, m, lane, mypos, s, false);
+            for (int s = q - 1; s >= p; --s) grc(S, m, col, lead, mypos, s, false);
         }
-        {  // tail sums of every slot from every row
+        if (lead) {  // tail sums of every slot from every row
             T acc = T(0);
-            S.Wt[32 * kLdW + lane] = T(0);
-            for (int r = 31; r >= 0; --r) {
-                const T z = S.R[r * kLd + lane];
+            S.Wt[MW * LD + col] = T(0);
+            for (int r = MW - 1; r >= 0; --r) {
+                const T z = S.R[r * LD + col];
                 acc = fma(z, z, acc);
-                S.Wt[r * kLdW + lane] = acc;
+                S.Wt[r * LD + col] = acc;
             }
         }
         __syncwarp();
-        // the sub-walk: families at the root, then one new prefix per swap
-        for (int a0 = d; a0 <= d + Q; ++a0) emit(S, g, w, lane, mypos, myvar, a0);
+        // the sub-walk: families at the root, then one new prefix per swap; each
+        // step's weights are loaded while the previous step's update runs
+        int s = nsteps > 0 ? d + ups_at(0) - 1 : 0;
+        T wf = family_weight(g, w, col, mypos, myvar, d);
+        for (int a0 = d; a0 <= d + Q; ++a0) {
+            T wn = T(0);
+            if (a0 < d + Q)
+                wn = family_weight(g, w, col, mypos, myvar, a0 + 1);
+            else if (nsteps > 0)
+                wn = family_weight(g, w, col, swapped(mypos, s), myvar, s + 1);
+            emit(S, g, col, ph, mypos, a0, wf);
+            wf = wn;
+        }
         for (int64_t t = 0; t < nsteps; ++t) {
-            const int s = d + upsilon_at(Q, t) - 1;
-            grc(S, m, lane, mypos, s, true);
-            emit(S, g, w, lane, mypos, myvar, s + 1);
+            grc(S, m, col, lead, mypos, s, true);
+            T wn = T(0);
+            int s_next = 0;
+            if (t + 1 < nsteps) {
+                s_next = d + ups_at(t + 1) - 1;
+                wn = family_weight(g, w, col, swapped(mypos, s_next), myvar, s_next + 1);
+            }
+            emit(S, g, col, ph, mypos, s + 1, wf);
+            wf = wn;
+            s = s_next;
         }
         // Gbar_sub = R_T^{-1} A R_T^{-T} in FP64, columns by final position
-        if (lane < m) {
+        if (lead && col < m) {
             S.var_at_pos[mypos] = myvar;
-            S.slot_at_pos[mypos] = lane;
+            S.slot_at_pos[mypos] = col;
         }
         __syncwarp();
-        const double diag = lane < m ? (double)S.R[lane * kLd + S.slot_at_pos[lane]] : 1.0;
+        const double diag = col < m ? (double)S.R[col * LD + S.slot_at_pos[col]] : 1.0;
         if (__any_sync(0xffffffffu, diag == 0.0)) {  // singular factor: flag, skip
             if (lane == 0) atomicOr(g.status, GBN_STATUS_RANK_DEFICIENT);
             continue;
         }
-        S.dinv[lane] = 1.0 / diag;  // every pivot's reciprocal at once (FP64 division is slow)
+        if (lead) S.dinv[col] = 1.0 / diag;  // every pivot's reciprocal at once
         __syncwarp();
-        if (lane < m) {  // Y = R_T^{-1} A, lane = column of A
+        if (lead && col < m) {  // Y = R_T^{-1} A, lane = column of A
             for (int p = m - 1; p >= 0; --p) {
-                double acc = (double)S.A[p * kLd + lane];
+                double acc = (double)S.A[p * LD + col];
                 for (int q = p + 1; q < m; ++q)
-                    acc -= (double)S.R[p * kLd + S.slot_at_pos[q]] * S.Y[q * kLdY + lane];
-                S.Y[p * kLdY + lane] = acc * S.dinv[p];
+                    acc -= (double)S.R[p * LD + S.slot_at_pos[q]] * S.Y[q * LD + col];
+                S.Y[p * LD + col] = acc * S.dinv[p];
             }
         }
         __syncwarp();
-        if (lane < m) {  // Gbar_sub = Y R_T^{-T}, lane = row, in place
+        if (lead && col < m) {  // Gbar_sub = Y R_T^{-T}, lane = row, in place
             for (int p = m - 1; p >= 0; --p) {
-                double acc = S.Y[lane * kLdY + p];
+                double acc = S.Y[col * LD + p];
                 for (int q = p + 1; q < m; ++q)
-                    acc -= (double)S.R[p * kLd + S.slot_at_pos[q]] * S.Y[lane * kLdY + q];
-                S.Y[lane * kLdY + p] = acc * S.dinv[p];
+                    acc -= (double)S.R[p * LD + S.slot_at_pos[q]] * S.Y[col * LD + q];
+                S.Y[col * LD + p] = acc * S.dinv[p];
             }
-            const int vr = S.var_at_pos[lane];
-            for (int q = 0; q < m; ++q) part[vr * m + S.var_at_pos[q]] += S.Y[lane * kLdY + q];
+            const int vr = S.var_at_pos[col];
+            for (int q = 0; q < m; ++q) part[vr * m + S.var_at_pos[q]] += S.Y[col * LD + q];
         }
         __syncwarp();
     }
 }
 
 // One dataset: warp wid takes sub-walks wid, wid + warps, ...
-template <typename T>
+template <typename T, int MW>
 __global__ void __launch_bounds__(32 * kBwdWarps) bwd_walk_kernel(BwdArgs g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    BwdWarpSmem<T>& S = reinterpret_cast<BwdWarpSmem<T>*>(smem_raw)[threadIdx.x >> 5];
+    BwdWarpSmem<T, MW>& S = reinterpret_cast<BwdWarpSmem<T, MW>*>(smem_raw)[threadIdx.x >> 5];
     grid_dep_wait();
     const int64_t wid = (int64_t)blockIdx.x * kBwdWarps + (threadIdx.x >> 5);
-    if (wid < g.warps) bwd_subwalks<T>(g, wid, g.warps, S);
+    if (wid < g.warps) bwd_subwalks<T, MW>(g, wid, g.warps, S);
 }
 
 // A batch: warp gw belongs to dataset d with warp_prefix[d] <= gw < warp_prefix[d+1].
-template <typename T>
+template <typename T, int MW>
 __global__ void __launch_bounds__(32 * kBwdWarps)
     bwd_walk_kernel_b(const BwdArgs* __restrict__ args, const int64_t* __restrict__ warp_prefix,
                       int B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    BwdWarpSmem<T>& S = reinterpret_cast<BwdWarpSmem<T>*>(smem_raw)[threadIdx.x >> 5];
+    BwdWarpSmem<T, MW>& S = reinterpret_cast<BwdWarpSmem<T, MW>*>(smem_raw)[threadIdx.x >> 5];
     const int64_t gw = (int64_t)blockIdx.x * kBwdWarps + (threadIdx.x >> 5);
     if (gw >= warp_prefix[B]) return;
     int lo = 0, hi = B;
@@ -299,7 +376,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps)
             hi = mid;
     }
     const BwdArgs& g = args[lo];  // read from global memory where used
-    bwd_subwalks<T>(g, gw - warp_prefix[lo], g.warps, S);
+    bwd_subwalks<T, MW>(g, gw - warp_prefix[lo], g.warps, S);
 }
 
 // Gsym = Gbar + Gbar^T from the per-warp sums (one warp per entry, lanes over
@@ -382,6 +459,7 @@ int make_bwd_plan(int64_t n, int32_t m, const givensbn_opts* opts, BwdPlan* b) {
     givensbn_default_opts(&o);
     if (opts) o = *opts;
     if (o.shard_count > 1) return GBN_ERR_OPTS;  // the gradient sums over every family
+    if (o.score == GBN_SCORE_BGE) return GBN_ERR_OPTS;  // the adjoint is that of n ln RSS
     const int qreq = o.q;
     o.q = 0;
     o.consumer_warps = 0;
@@ -405,21 +483,21 @@ int make_bwd_plan(int64_t n, int32_t m, const givensbn_opts* opts, BwdPlan* b) {
     return GBN_OK;
 }
 
-template <typename T>
-int launch_bwd(const BwdPlan& b, const double* X, const void* w, double* grad, char* ws,
-               cudaStream_t stream) {
+template <typename T, int MW>
+int launch_bwd_w(const BwdPlan& b, const double* X, const void* w, double* grad, char* ws,
+                 cudaStream_t stream) {
     const Plan& p = b.p;
     BwdArgs g = bwd_args(p, ws, X, w, grad, b.Qb, b.n_sub, b.warps,
                          reinterpret_cast<double*>(ws + b.off_partials),
                          reinterpret_cast<double*>(ws + b.off_gsym),
                          reinterpret_cast<double*>(ws + b.off_muv));
-    const size_t smem = sizeof(BwdWarpSmem<T>) * kBwdWarps;
-    if (cudaFuncSetAttribute(bwd_walk_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = sizeof(BwdWarpSmem<T, MW>) * kBwdWarps;
+    if (cudaFuncSetAttribute(bwd_walk_kernel<T, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return GBN_ERR_CUDA;
     const unsigned blocks = (unsigned)((b.warps + kBwdWarps - 1) / kBwdWarps);
     const cudaError_t e[] = {
-        launch_dep(bwd_walk_kernel<T>, dim3(blocks), dim3(32 * kBwdWarps), smem, stream, g),
+        launch_dep(bwd_walk_kernel<T, MW>, dim3(blocks), dim3(32 * kBwdWarps), smem, stream, g),
         launch_dep(bwd_reduce_kernel, dim3(8), dim3(256), 0, stream, (const double*)g.partials,
                    g.warps, p.m, g.mu_plan, p, g.gsym, g.mu_var),
         launch_dep(bwd_grad_kernel, dim3(304), dim3(256), 0, stream, X, p.n, p.m,
@@ -430,16 +508,35 @@ int launch_bwd(const BwdPlan& b, const double* X, const void* w, double* grad, c
 }
 
 template <typename T>
-int launch_bwd_batched_t(const BwdArgs* args, const int64_t* warp_prefix, int B,
-                         int64_t total_warps, cudaStream_t stream) {
-    const size_t smem = sizeof(BwdWarpSmem<T>) * kBwdWarps;
-    if (cudaFuncSetAttribute(bwd_walk_kernel_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+int launch_bwd(const BwdPlan& b, const double* X, const void* w, double* grad, char* ws,
+               cudaStream_t stream) {
+    return b.p.m <= 16 ? launch_bwd_w<T, 16>(b, X, w, grad, ws, stream)
+                       : launch_bwd_w<T, 32>(b, X, w, grad, ws, stream);
+}
+
+// The walk over datasets [0, B) of args with one width.
+template <typename T, int MW>
+int launch_bwd_walk_group(const BwdArgs* args, const int64_t* warp_prefix, int B, int64_t warps,
+                          cudaStream_t stream) {
+    if (B == 0 || warps == 0) return GBN_OK;
+    const size_t smem = sizeof(BwdWarpSmem<T, MW>) * kBwdWarps;
+    if (cudaFuncSetAttribute(bwd_walk_kernel_b<T, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return GBN_ERR_CUDA;
-    const unsigned blocks = (unsigned)((total_warps + kBwdWarps - 1) / kBwdWarps);
+    const unsigned blocks = (unsigned)((warps + kBwdWarps - 1) / kBwdWarps);
+    return launch_rc(launch_plain(bwd_walk_kernel_b<T, MW>, dim3(blocks), dim3(32 * kBwdWarps),
+                                  smem, stream, args, warp_prefix, B));
+}
+
+template <typename T>
+int launch_bwd_batched_t(const BwdArgs* args, const int64_t* prefix, int B, int B_narrow,
+                         int64_t warps_narrow, int64_t warps_wide, cudaStream_t stream) {
+    int rc = launch_bwd_walk_group<T, 16>(args, prefix, B_narrow, warps_narrow, stream);
+    if (rc == GBN_OK)
+        rc = launch_bwd_walk_group<T, 32>(args + B_narrow, prefix + B_narrow + 1, B - B_narrow,
+                                          warps_wide, stream);
+    if (rc) return rc;
     const cudaError_t e[] = {
-        launch_plain(bwd_walk_kernel_b<T>, dim3(blocks), dim3(32 * kBwdWarps), smem, stream, args,
-                     warp_prefix, B),
         launch_plain(bwd_reduce_kernel_b, dim3(4, (unsigned)B), dim3(256), 0, stream, args),
         launch_plain(bwd_grad_kernel_b, dim3(32, (unsigned)B), dim3(256), 0, stream, args)};
     for (cudaError_t x : e)
@@ -450,7 +547,7 @@ int launch_bwd_batched_t(const BwdArgs* args, const int64_t* warp_prefix, int B,
 }  // namespace
 
 int bwd_subwalk_plan(int m, int q_requested, int* Qb, int64_t* n_sub, int64_t* warps) {
-    int q = q_requested > 0 ? q_requested : m - 10;
+    int q = q_requested > 0 ? q_requested : m - 9;
     if (q_requested <= 0) {
         if (q < 2) q = 2;
         if (q > m) q = m;
@@ -486,10 +583,13 @@ BwdArgs bwd_args(const Plan& p, char* ws, const double* X, const void* w, double
     return g;
 }
 
-int launch_bwd_batched(const BwdArgs* args, const int64_t* warp_prefix, int B, int64_t total_warps,
-                       int precision, cudaStream_t stream) {
-    return precision ? launch_bwd_batched_t<double>(args, warp_prefix, B, total_warps, stream)
-                     : launch_bwd_batched_t<float>(args, warp_prefix, B, total_warps, stream);
+int launch_bwd_batched(const BwdArgs* args, const int64_t* prefix, int B, int B_narrow,
+                       int64_t warps_narrow, int64_t warps_wide, int precision,
+                       cudaStream_t stream) {
+    return precision ? launch_bwd_batched_t<double>(args, prefix, B, B_narrow, warps_narrow,
+                                                    warps_wide, stream)
+                     : launch_bwd_batched_t<float>(args, prefix, B, B_narrow, warps_narrow,
+                                                   warps_wide, stream);
 }
 
 }  // namespace gbn

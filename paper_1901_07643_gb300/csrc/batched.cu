@@ -83,6 +83,7 @@ int plan_batch(const int64_t* ns, const int32_t* ms, int32_t B, const givensbn_o
     }
     o.q = Q;
     o.fixup_tau = 0.0;  // the FP64 fix-up pass belongs to the single-dataset entry point
+    if (o.score == GBN_SCORE_BGE) return GBN_ERR_OPTS;  // the BGe pass: single datasets only
     L->plans.resize(B);
     for (int b = 0; b < B; ++b) {
         const int rc = make_plan(ns[b], ms[b], &o, &L->plans[b]);
@@ -265,7 +266,6 @@ struct BwdBatchLayout {
     std::vector<int64_t> n_sub, warps;
     std::vector<size_t> off_partials, off_gsym, off_muv;
     size_t off_args = 0, off_prefix = 0, total = 0;
-    int64_t total_warps = 0;
 };
 
 int plan_bwd_batch(const int64_t* ns, const int32_t* ms, int32_t B, const givensbn_opts* opts,
@@ -288,7 +288,6 @@ int plan_bwd_batch(const int64_t* ns, const int32_t* ms, int32_t B, const givens
     K->off_gsym.resize(B);
     K->off_muv.resize(B);
     size_t off = K->L.total;
-    K->total_warps = 0;
     for (int b = 0; b < B; ++b) {
         if ((rc = bwd_subwalk_plan(ms[b], qreq, &K->Qb[b], &K->n_sub[b], &K->warps[b]))) return rc;
         const size_t m = (size_t)ms[b];
@@ -298,12 +297,11 @@ int plan_bwd_batch(const int64_t* ns, const int32_t* ms, int32_t B, const givens
         off = up256(off + sizeof(double) * m * m);
         K->off_muv[b] = off;
         off = up256(off + sizeof(double) * 32);
-        K->total_warps += K->warps[b];
     }
     K->off_args = off;
     off = up256(off + sizeof(BwdArgs) * B);
     K->off_prefix = off;
-    off = up256(off + sizeof(int64_t) * (B + 1));
+    off = up256(off + sizeof(int64_t) * (B + 2));  // one warp prefix per width group
     K->total = off;
     return GBN_OK;
 }
@@ -363,17 +361,26 @@ extern "C" int score_all_families_backward_batched(const double* const* Xs, cons
     memcpy(host.data() + L.off_ws, ws.data(), sizeof(void*) * B);
     memcpy(host.data() + L.off_out, outp.data(), sizeof(void*) * B);
     if ((rc = upload(host, base, stream))) return rc;
-    // ... and the adjoint's: per-dataset arguments and the prefix of warps
+    // ... and the adjoint's: per-dataset arguments, datasets with m <= 16 first (the
+    // 16-column kernel), each width group with its own prefix of warps
     std::vector<unsigned char> tail(K.total - K.off_args, 0);
     BwdArgs* args = reinterpret_cast<BwdArgs*>(tail.data());
-    int64_t* warp_prefix = reinterpret_cast<int64_t*>(tail.data() + (K.off_prefix - K.off_args));
-    warp_prefix[0] = 0;
+    int64_t* prefix = reinterpret_cast<int64_t*>(tail.data() + (K.off_prefix - K.off_args));
+    int B_narrow = 0;
+    for (int b = 0; b < B; ++b) B_narrow += ms[b] <= 16;
+    int64_t warps_group[2] = {0, 0};
+    int slot[2] = {0, B_narrow};
+    prefix[0] = 0;
+    prefix[B_narrow + 1] = 0;
     for (int b = 0; b < B; ++b) {
-        args[b] = bwd_args(L.plans[b], ws[b], X[b], weights[b], grads[b], K.Qb[b], K.n_sub[b],
+        const int grp = ms[b] <= 16 ? 0 : 1;
+        const int i = slot[grp]++;
+        args[i] = bwd_args(L.plans[b], ws[b], X[b], weights[b], grads[b], K.Qb[b], K.n_sub[b],
                            K.warps[b], reinterpret_cast<double*>(base + K.off_partials[b]),
                            reinterpret_cast<double*>(base + K.off_gsym[b]),
                            reinterpret_cast<double*>(base + K.off_muv[b]));
-        warp_prefix[b + 1] = warp_prefix[b] + K.warps[b];
+        warps_group[grp] += K.warps[b];
+        prefix[i + grp + 1] = prefix[i + grp] + K.warps[b];
     }
     if ((rc = upload(tail, base + K.off_args, stream))) return rc;
     BatchView v;
@@ -391,6 +398,6 @@ extern "C" int score_all_families_backward_batched(const double* const* Xs, cons
     for (int b = 0; b < B; ++b) max_m = std::max(max_m, L.plans[b].m);
     if ((rc = launch_r0_batched(v, L.total_panels, max_m, stream))) return rc;
     return launch_bwd_batched(reinterpret_cast<const BwdArgs*>(base + K.off_args),
-                              reinterpret_cast<const int64_t*>(base + K.off_prefix), B,
-                              K.total_warps, precision, stream);
+                              reinterpret_cast<const int64_t*>(base + K.off_prefix), B, B_narrow,
+                              warps_group[0], warps_group[1], precision, stream);
 }

@@ -134,6 +134,7 @@ extern "C" int givensbn_coefficients_workspace_size(int64_t n, int32_t m, const 
     o.precision = 0;
     o.q = 0;
     o.tune_cache = nullptr;
+    o.score = GBN_SCORE_BIC;  // coefficients do not depend on the score
     Plan p;
     const int rc = make_plan(n, m, &o, &p);
     if (rc) return rc;
@@ -150,6 +151,7 @@ extern "C" int givensbn_family_coefficients(const double* X, int64_t n, int32_t 
     o.precision = 0;
     o.q = 0;
     o.tune_cache = nullptr;
+    o.score = GBN_SCORE_BIC;  // coefficients do not depend on the score
     o.fixup_tau = 0.0;
     Plan p;
     int rc = make_plan(n, m, &o, &p);

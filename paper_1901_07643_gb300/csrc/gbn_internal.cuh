@@ -75,6 +75,11 @@ struct Plan {
     double lam = 0.0;        // score penalty per parent (ln n: BIC, 2: AIC, or the caller's)
     int kmax = 0;            // in-degree bound: families with more parents are not written (m-1: none)
     long long watchdog_ns = 0;  // bound on every wait between the warps of a walk block
+    // BGe score: the walk runs over a factor of t I + S_n and stores n ln(rho / n); a
+    // pass over the table then forms the BGe scores (L: 2^m elements at off_bge)
+    int bge = 0;
+    double bge_t = 0.0, bge_alpha_mu = 0.0, bge_alpha_w = 0.0;
+    size_t off_bge = 0;
     __host__ __device__ bool sharded() const { return cta_begin != 0 || n_cta != n_cta_total; }
 };
 
@@ -101,6 +106,10 @@ int launch_walk(const Plan& p, char* ws, void* out, cudaStream_t stream);
 // possible RSS is tiny before the walk, recompute the listed families after it.
 int launch_fix_flags(const Plan& p, char* ws, cudaStream_t stream);
 int launch_fixup(const Plan& p, char* ws, void* out, cudaStream_t stream);
+// BGe: R0 <- the factor of R0^T R0 + t I (before the flags and roots), and the
+// pass that turns the walk's table into BGe scores (after the fix-up).
+int launch_bge_prior(const Plan& p, char* ws, cudaStream_t stream);
+int launch_bge_finalize(const Plan& p, char* ws, void* out, cudaStream_t stream);
 // The whole single-dataset pipeline (R0, flags, roots, walk, fix-up).
 int run_pipeline(const Plan& p, const double* X, char* ws, void* out, cudaStream_t stream,
                  void* stage_events);
@@ -227,8 +236,13 @@ struct BwdArgs {
 int bwd_subwalk_plan(int m, int q_requested, int* Qb, int64_t* n_sub, int64_t* warps);
 BwdArgs bwd_args(const Plan& p, char* ws, const double* X, const void* w, double* grad, int Qb,
                  int64_t n_sub, int64_t warps, double* partials, double* gsym, double* mu_var);
-int launch_bwd_batched(const BwdArgs* args, const int64_t* warp_prefix, int B, int64_t total_warps,
-                       int precision, cudaStream_t stream);
+// The adjoint walk of a batch: args[0, B_narrow) hold datasets with m <= 16
+// (the 16-column kernel; warp prefix at prefix[0, B_narrow]), args[B_narrow, B)
+// the rest (warp prefix at prefix[B_narrow + 1, B + 1]); then the reduction and
+// the gradient of every dataset.
+int launch_bwd_batched(const BwdArgs* args, const int64_t* prefix, int B, int B_narrow,
+                       int64_t warps_narrow, int64_t warps_wide, int precision,
+                       cudaStream_t stream);
 int launch_roots_batched(const BatchView& v, int64_t total_cta, int Q, int max_w,
                          size_t max_stride, int precision, cudaStream_t stream);
 int launch_walk_batched(const BatchView& v, int64_t total_cta, int Q, int precision, bool coverage,
