@@ -38,8 +38,9 @@ WALK_SOURCES = ["paper_1901_07643_gb300/csrc/walk3.cuh", "paper_1901_07643_gb300
                 "paper_1901_07643_gb300/csrc/walk_dispatch.cu",
                 "paper_1901_07643_gb300/csrc/gbn_internal.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "walk_traffic.json")
-LAUNCHES_PER_STEP = 14  # colsum, mean, (gram, gram sum, cholesky) x2, fix-up flags,
-                        # roots top + leaves, walk, fix-up scan + solve
+LAUNCHES_PER_STEP = 16  # colsum, mean, (gram, gram sum, cholesky) x2, column scaling,
+                        # fix-up flags, roots top + leaves, walk, fix-up scan + solve,
+                        # score correction of scaled columns
 
 
 def _args():

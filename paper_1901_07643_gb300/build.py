@@ -43,7 +43,7 @@ def _jobs(obj_dir=OBJ, extra=()):
     src_common = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(INCLUDE, "givensbn.h")]
     jobs = []
     for name in ("r0", "roots", "api", "walk_dispatch", "noalloc", "backward", "batched", "fixup",
-                 "tune", "coef", "search", "peaks", "bge"):
+                 "tune", "coef", "search", "peaks", "bge", "scale"):
         src = os.path.join(CSRC, name + ".cu")
         jobs.append((os.path.join(obj_dir, name + ".o"), [src], [src] + src_common, list(extra)))
     inst = os.path.join(CSRC, "walk_inst.cu")

@@ -167,6 +167,11 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
         p->off_bge = off;
         off = align_up(off + es * ((size_t)1 << m), 256);
     }
+    if (precision == 0 && !p->coverage) {
+        p->scale = 1;
+        p->off_scale = off;
+        off = align_up(off + sizeof(int) * 33, 256);
+    }
     p->total_bytes = off;
     return GBN_OK;
 }
@@ -207,6 +212,7 @@ int run_pipeline(const Plan& p, const double* X, char* ws, void* out, cudaStream
     if (ev && cudaEventRecord(ev[0], stream) != cudaSuccess) return GBN_ERR_CUDA;
     int rc = launch_r0(p, X, ws, stream);
     if (rc == GBN_OK && p.bge) rc = launch_bge_prior(p, ws, stream);
+    if (rc == GBN_OK && p.scale) rc = launch_scale_r0(p, ws, stream);
     if (rc == GBN_OK && p.fix_cap) rc = launch_fix_flags(p, ws, stream);
     if ((rc = checked_stage("r0", rc, p, ws, stream))) return rc;
     if (ev && cudaEventRecord(ev[1], stream) != cudaSuccess) return GBN_ERR_CUDA;
@@ -219,6 +225,10 @@ int run_pipeline(const Plan& p, const double* X, char* ws, void* out, cudaStream
     if (p.fix_cap) {
         rc = launch_fixup(p, ws, out, stream);
         if ((rc = checked_stage("fixup", rc, p, ws, stream))) return rc;
+    }
+    if (p.scale) {
+        rc = launch_unscale(p, ws, out, stream);
+        if ((rc = checked_stage("unscale", rc, p, ws, stream))) return rc;
     }
     if (p.bge) {
         rc = launch_bge_finalize(p, ws, out, stream);

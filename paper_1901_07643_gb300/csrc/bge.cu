@@ -119,6 +119,20 @@ __global__ void __launch_bounds__(256) bge_logdet_kernel(const Plan p, const T* 
                  (int64_t)gridDim.x * blockDim.x, (T)co.inv_n, (T)co.ln_n);
 }
 
+__device__ __forceinline__ uint64_t parent_set(int c, uint64_t cm) {
+    return (cm & ((1ull << c) - 1ull)) | ((cm >> c) << (c + 1));
+}
+
+template <typename T>
+__device__ __forceinline__ T bge_value(T v, T Ls, int l, const T* K, const T* a, T inv_n, T ln_n) {
+    return fma(-a[l], ln_rho(v, inv_n, ln_n), fma(T(-0.5), Ls, K[l]));
+}
+
+// Every written slot rewritten in place.  FP32 with m >= 3: four consecutive slots per
+// thread (one child, parent masks 4i .. 4i + 3), one 16-byte load and store of the table,
+// and for children c >= 2 one 16-byte load of L (the two low mask bits are below c, so the
+// four parent sets are consecutive and start at a multiple of 4).  A slot above the
+// in-degree bound is stored back unchanged.
 template <typename T>
 __global__ void __launch_bounds__(256) bge_finalize_kernel(const Plan p, T* __restrict__ table,
                                                            const T* __restrict__ L,
@@ -134,14 +148,42 @@ __global__ void __launch_bounds__(256) bge_finalize_kernel(const Plan p, T* __re
     const int64_t half = (int64_t)1 << (m - 1);
     const int64_t total = (int64_t)m * half;
     const T inv_n = (T)co.inv_n, ln_n = (T)co.ln_n;
-    for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < total;
-         slot += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if constexpr (sizeof(T) == 4) {
+        if (m >= 3) {
+            float4* t4 = reinterpret_cast<float4*>(table);
+            for (int64_t qd = tid; qd < total / 4; qd += stride) {
+                const int64_t slot = qd * 4;
+                const int c = (int)(slot >> (m - 1));
+                const uint64_t cm = (uint64_t)(slot & (half - 1));
+                const uint64_t S = parent_set(c, cm);
+                float4 v = t4[qd];
+                float Ls[4];
+                if (c >= 2) {
+                    const float4 l4 = reinterpret_cast<const float4*>(L)[S >> 2];
+                    Ls[0] = l4.x; Ls[1] = l4.y; Ls[2] = l4.z; Ls[3] = l4.w;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) Ls[i] = L[parent_set(c, cm + i)];
+                }
+                float* vv = reinterpret_cast<float*>(&v);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int l = __popcll(cm + i);
+                    if (l <= p.kmax) vv[i] = bge_value(vv[i], Ls[i], l, K, a, inv_n, ln_n);
+                }
+                t4[qd] = v;
+            }
+            return;
+        }
+    }
+    for (int64_t slot = tid; slot < total; slot += stride) {
         const int c = (int)(slot >> (m - 1));
         const uint64_t cm = (uint64_t)(slot & (half - 1));
         const int l = __popcll(cm);
         if (l > p.kmax) continue;
-        const uint64_t S = (cm & ((1ull << c) - 1ull)) | ((cm >> c) << (c + 1));
-        table[slot] = fma(-a[l], ln_rho(table[slot], inv_n, ln_n), fma(T(-0.5), L[S], K[l]));
+        table[slot] = bge_value(table[slot], L[parent_set(c, cm)], l, K, a, inv_n, ln_n);
     }
 }
 
@@ -177,7 +219,7 @@ int launch_finalize_t(const Plan& p, char* ws, T* out, cudaStream_t stream) {
             return GBN_ERR_CUDA;
     }
     const int64_t total = (int64_t)m << (m - 1);
-    const int64_t want = (total + 255) / 256;
+    const int64_t want = (total / 4 + 255) / 256 + 1;
     const unsigned nb = (unsigned)(want < (int64_t)sms * 16 ? want : (int64_t)sms * 16);
     if (launch_dep(bge_finalize_kernel<T>, dim3(nb), dim3(256), 0, stream, p, out, (const T*)L,
                    co) != cudaSuccess)

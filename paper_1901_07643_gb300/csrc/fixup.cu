@@ -62,18 +62,6 @@ __global__ void __launch_bounds__(1024) fix_flags_kernel(const Plan p, char* ws)
 
 constexpr int kScanBlocksPerChild = 64;
 
-// Whether this call wrote slot s (compressed parent mask) of child c: the
-// family's parent count is within the bound, and with sharding its sub-walk
-// CTA, (S & H) >> W with H the fixed variables 0..k-1, is in the call's range.
-__device__ __forceinline__ bool slot_written(const Plan& p, int c, int64_t s) {
-    const uint64_t cs = (uint64_t)s;
-    if (__popcll(cs) > p.kmax) return false;
-    if (!p.sharded()) return true;
-    const uint64_t S = (cs & ((1ull << c) - 1ull)) | ((cs >> c) << (c + 1));
-    const int64_t g = (int64_t)((S & ((1ull << p.k) - 1ull)) >> p.W);
-    return g >= p.cta_begin && g < p.cta_begin + p.n_cta;
-}
-
 // List the families of flagged children whose score is below the threshold.
 __global__ void fix_scan_kernel(const Plan p, char* ws, const float* __restrict__ out) {
     grid_dep_wait();

@@ -80,8 +80,25 @@ struct Plan {
     int bge = 0;
     double bge_t = 0.0, bge_alpha_mu = 0.0, bge_alpha_w = 0.0;
     size_t off_bge = 0;
+    // FP32 walk: R0's columns scaled by powers of two into a safe range before the
+    // FP32 stages, the scores of scaled children corrected after the walk
+    // (exponents by variable and an any-scaled word at off_scale)
+    int scale = 0;
+    size_t off_scale = 0;
     __host__ __device__ bool sharded() const { return cta_begin != 0 || n_cta != n_cta_total; }
 };
+
+// Whether this call wrote slot s (compressed parent mask) of child c: the
+// family's parent count is within the bound, and with sharding its sub-walk
+// CTA, (S & H) >> W with H the fixed variables 0..k-1, is in the call's range.
+__device__ __forceinline__ bool slot_written(const Plan& p, int c, int64_t s) {
+    const uint64_t cs = (uint64_t)s;
+    if (__popcll(cs) > p.kmax) return false;
+    if (!p.sharded()) return true;
+    const uint64_t S = (cs & ((1ull << c) - 1ull)) | ((cs >> c) << (c + 1));
+    const int64_t g = (int64_t)((S & ((1ull << p.k) - 1ull)) >> p.W);
+    return g >= p.cta_begin && g < p.cta_begin + p.n_cta;
+}
 
 // A wait inside the walk that lasts this long means the schedule is broken.
 constexpr long long kWatchdogNs = 2000000000ll;
@@ -110,6 +127,10 @@ int launch_fixup(const Plan& p, char* ws, void* out, cudaStream_t stream);
 // pass that turns the walk's table into BGe scores (after the fix-up).
 int launch_bge_prior(const Plan& p, char* ws, cudaStream_t stream);
 int launch_bge_finalize(const Plan& p, char* ws, void* out, cudaStream_t stream);
+// FP32 walk: equilibrate R0's columns (after the R0 stage) and correct the
+// scaled children's scores (after the fix-up).
+int launch_scale_r0(const Plan& p, char* ws, cudaStream_t stream);
+int launch_unscale(const Plan& p, char* ws, void* out, cudaStream_t stream);
 // The whole single-dataset pipeline (R0, flags, roots, walk, fix-up).
 int run_pipeline(const Plan& p, const double* X, char* ws, void* out, cudaStream_t stream,
                  void* stage_events);
