@@ -46,6 +46,7 @@ struct BatchLayout {
     // table offsets (from the workspace base)
     size_t off_cta_prefix = 0, off_panel_prefix = 0, off_dataset_of = 0, off_plans = 0,
            off_X = 0, off_ws = 0, off_out = 0, off_args = 0;
+    size_t off_panel_pos = 0, off_cta_pos = 0;  // position maps, filled on the device
 };
 
 int plan_batch(const int64_t* ns, const int32_t* ms, int32_t B, const givensbn_opts* opts,
@@ -121,16 +122,22 @@ int plan_batch(const int64_t* ns, const int32_t* ms, int32_t B, const givensbn_o
     L->off_args = off;
     off = up256(off + std::max(sizeof(WalkArgs<float>), sizeof(WalkArgs<double>)) * B);
     L->table_bytes = off;
-    L->ws_off.resize(B);
     L->total_cta = 0;
     L->total_panels = 0;
     for (int b = 0; b < B; ++b) {
-        L->ws_off[b] = off;
-        off = up256(off + L->plans[b].total_bytes);
         L->total_cta += L->plans[b].n_cta;
         L->total_panels += L->plans[b].panels;
     }
     if (L->total_cta > 0x7fffffff || L->total_panels > 0x7fffffff) return GBN_ERR_BATCH;
+    L->off_panel_pos = off;
+    off = up256(off + sizeof(int32_t) * (size_t)L->total_panels);
+    L->off_cta_pos = off;
+    off = up256(off + sizeof(int32_t) * (size_t)(L->total_cta > 0 ? L->total_cta : 1));
+    L->ws_off.resize(B);
+    for (int b = 0; b < B; ++b) {
+        L->ws_off[b] = off;
+        off = up256(off + L->plans[b].total_bytes);
+    }
     L->total = off;
     return GBN_OK;
 }
@@ -233,6 +240,8 @@ extern "C" int score_all_families_batched(const double* const* Xs, const int64_t
     v.cta_prefix = reinterpret_cast<const int64_t*>(base + L.off_cta_prefix);
     v.panel_prefix = reinterpret_cast<const int64_t*>(base + L.off_panel_prefix);
     v.dataset_of = reinterpret_cast<const int32_t*>(base + L.off_dataset_of);
+    v.panel_pos = reinterpret_cast<int32_t*>(base + L.off_panel_pos);
+    v.cta_pos = reinterpret_cast<int32_t*>(base + L.off_cta_pos);
     v.plans = reinterpret_cast<const Plan*>(base + L.off_plans);
     v.X = reinterpret_cast<const double* const*>(base + L.off_X);
     v.ws = reinterpret_cast<char* const*>(base + L.off_ws);
@@ -388,6 +397,8 @@ extern "C" int score_all_families_backward_batched(const double* const* Xs, cons
     v.cta_prefix = reinterpret_cast<const int64_t*>(base + L.off_cta_prefix);
     v.panel_prefix = reinterpret_cast<const int64_t*>(base + L.off_panel_prefix);
     v.dataset_of = reinterpret_cast<const int32_t*>(base + L.off_dataset_of);
+    v.panel_pos = reinterpret_cast<int32_t*>(base + L.off_panel_pos);
+    v.cta_pos = reinterpret_cast<int32_t*>(base + L.off_cta_pos);
     v.plans = reinterpret_cast<const Plan*>(base + L.off_plans);
     v.X = reinterpret_cast<const double* const*>(base + L.off_X);
     v.ws = reinterpret_cast<char* const*>(base + L.off_ws);

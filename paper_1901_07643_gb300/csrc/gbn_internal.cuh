@@ -165,6 +165,8 @@ struct BatchView {
     const int64_t* cta_prefix = nullptr;    // B+1: sub-walk CTAs (roots, walk)
     const int64_t* panel_prefix = nullptr;  // B+1: row panels (R0 passes)
     const int32_t* dataset_of = nullptr;    // launch position -> dataset index
+    int32_t* panel_pos = nullptr;           // global row panel -> launch position
+    int32_t* cta_pos = nullptr;             // global sub-walk CTA -> launch position
     const Plan* plans = nullptr;
     const double* const* X = nullptr;
     char* const* ws = nullptr;              // per-dataset workspace region
@@ -173,8 +175,6 @@ struct BatchView {
     int pairs = 0;                          // every dataset takes the paired FP32 walk
 };
 
-// Dataset index for global block bx: the launch position l with
-// prefix[l] <= bx < prefix[l+1]; local = bx - prefix[l].
 // Programmatic dependent launch.  A kernel launched with launch_dep may be
 // dispatched while the previous kernel on the stream finishes; every such
 // kernel calls grid_dep_wait() before anything else, which returns once the
@@ -218,20 +218,16 @@ inline cudaError_t launch_plain(void (*kernel)(KArgs...), dim3 grid, dim3 block,
 }
 inline int launch_rc(cudaError_t e) { return e == cudaSuccess ? GBN_OK : GBN_ERR_CUDA; }
 
-__device__ __forceinline__ int batch_locate(const BatchView& v, const int64_t* prefix, int64_t bx,
-                                            int64_t& local) {
-    int lo = 0, hi = v.B;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (prefix[mid] <= bx)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    local = bx - prefix[lo];
-    return v.dataset_of[lo];
+__device__ __forceinline__ int batch_locate(const BatchView& v, const int64_t* prefix,
+                                            const int32_t* pos, int64_t bx, int64_t& local) {
+    const int l = pos[bx];  // filled from the prefix once per call (launch_r0_batched)
+    local = bx - prefix[l];
+    return v.dataset_of[l];
 }
 
+// Dataset index for global block bx: the launch position l with
+// prefix[l] <= bx < prefix[l+1] (read from the position map pos, which the
+// first kernel of launch_r0_batched fills for panels and CTAs); local = bx - prefix[l].
 int launch_r0_batched(const BatchView& v, int64_t total_panels, int max_m, cudaStream_t stream);
 
 // The adjoint walk of one dataset (backward.cu): its R0, weights, per-warp

@@ -344,6 +344,15 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel(const Plan p, char* 
         chol_body(q.gsum, p.m, nullptr, q.r1, q.r1inv, q.status, q.chk);
 }
 
+// A batch: the position maps (block -> launch position) of panels (y = 0) and of
+// sub-walk CTAs (y = 1), one block per launch position.
+__global__ void batch_pos_kernel(const BatchView v) {
+    const int l = blockIdx.x;
+    const int64_t* prefix = blockIdx.y ? v.cta_prefix : v.panel_prefix;
+    int32_t* pos = blockIdx.y ? v.cta_pos : v.panel_pos;
+    for (int64_t i = prefix[l] + threadIdx.x; i < prefix[l + 1]; i += blockDim.x) pos[i] = l;
+}
+
 // A batch: blocks are mapped to (dataset, panel) through the prefix of panels.
 __global__ void status_clear_kernel_b(const BatchView v) {
     const int d = blockIdx.x;
@@ -352,7 +361,7 @@ __global__ void status_clear_kernel_b(const BatchView v) {
 }
 __global__ void colsum_kernel_b(const BatchView v) {
     int64_t local;
-    const int d = batch_locate(v, v.panel_prefix, blockIdx.x, local);
+    const int d = batch_locate(v, v.panel_prefix, v.panel_pos, blockIdx.x, local);
     const Plan& p = v.plans[d];
     if (!p.center) return;
     const R0Ptrs q = r0_ptrs(p, v.ws[d]);
@@ -366,7 +375,7 @@ __global__ void __launch_bounds__(kRedThreads) mean_kernel_b(const BatchView v) 
 }
 __global__ void gram_kernel_b(const BatchView v, int pass) {
     int64_t local;
-    const int d = batch_locate(v, v.panel_prefix, blockIdx.x, local);
+    const int d = batch_locate(v, v.panel_prefix, v.panel_pos, blockIdx.x, local);
     const Plan& p = v.plans[d];
     const R0Ptrs q = r0_ptrs(p, v.ws[d]);
     gram_body((int)local, v.X[d], p.n, p.m, p.rows_per_panel, q.mu, p.panels,
@@ -415,6 +424,7 @@ int launch_r0_batched(const BatchView& v, int64_t total_panels, int max_m, cudaS
     const unsigned B = (unsigned)v.B, P = (unsigned)total_panels;
     const dim3 sum_grid((unsigned)((max_m * (max_m + 1) / 2 + 31) / 32), B);
     const cudaError_t e[] = {
+        launch_plain(batch_pos_kernel, dim3(B, 2), dim3(256), 0, stream, v),
         launch_plain(status_clear_kernel_b, dim3(B), dim3(64), 0, stream, v),
         launch_plain(colsum_kernel_b, dim3(P), dim3(256), 0, stream, v),
         launch_plain(mean_kernel_b, dim3(B), dim3(kRedThreads), 0, stream, v),

@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(32 * kTopWarps) roots_top_kernel_b(const Batch
     const int64_t g = (int64_t)blockIdx.x * kTopWarps + warp;
     if (g >= v.cta_prefix[v.B]) return;
     int64_t local;
-    const int d = batch_locate(v, v.cta_prefix, g, local);
+    const int d = batch_locate(v, v.cta_prefix, v.cta_pos, g, local);
     const Plan& p = v.plans[d];
     char* ws = v.ws[d];
     top_body<T>(reinterpret_cast<const double*>(ws + p.off_r0), p, top_nodes<T>(p, ws),
@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(32 * kDfsWarps) roots_leaves_kernel_b(const Ba
     const int64_t g = (int64_t)blockIdx.x * kDfsWarps + warp;
     if (g >= v.cta_prefix[v.B]) return;
     int64_t local;
-    const int d = batch_locate(v, v.cta_prefix, g, local);
+    const int d = batch_locate(v, v.cta_prefix, v.cta_pos, g, local);
     const Plan& p = v.plans[d];
     char* ws = v.ws[d];
     T* stack = reinterpret_cast<T*>(smem_raw) + warp * warp_smem_elems(Q, max_w, max_stride);
@@ -819,7 +819,7 @@ __global__ void __launch_bounds__(32 * kDfsWarps, 7)
     const int64_t g = gw >> 1;
     if (g >= v.cta_prefix[v.B]) return;
     int64_t local;
-    const int d = batch_locate(v, v.cta_prefix, g, local);
+    const int d = batch_locate(v, v.cta_prefix, v.cta_pos, g, local);
     const Plan& p = v.plans[d];
     char* ws = v.ws[d];
     T* stg = reinterpret_cast<T*>(smem_raw) + warp * stage_elems(max_stride);
