@@ -32,6 +32,7 @@ namespace gbn {
 constexpr int kCheckOffset = 64;    // byte offset of the check record in the status block
 constexpr int kTimingOffset = 128;  // byte offset of the timing counters (timing builds)
 constexpr int kFixCountOffset = 16; // byte offset of the fix-up list length (unsigned)
+constexpr int kR0OnePassOffset = 32; // byte offset of the R0 stage's one-pass flag (int)
 constexpr int kFixCap = 1 << 18;    // fix-up list capacity (families)
 
 constexpr int kMaxQ = 9;     // largest sub-walk size compiled (FP32; the tape lives in shared memory)

@@ -4,6 +4,13 @@
 //   pass 1: G1 = Xc^T Xc (row panels, then summed over panels), R1 = chol(G1)
 //   pass 2: Q1 = Xc R1^{-1} (explicit triangular inverse), G2 = Q1^T Q1,
 //           R2 = chol(G2), R0 = R2 R1.
+// Pass 2 exists for ill-conditioned data: an RSS read from R1 has relative
+// error about eps ||x_c||^2 / RSS, the RSS of the explicitly orthogonalised Q1
+// about eps ||x_c|| / sqrt(RSS).  When every column's smallest possible RSS
+// (on all the other columns, 1 / (G1^{-1})_cc) is at least kOnePassRatio of its
+// sum of squares, R1 is already that accurate (eps / 1e-3, about 1e-13): the
+// pass-1 Cholesky kernel then writes R0 = R1 and raises a flag in the status
+// block, and the pass-2 kernels return at once.
 // Columns are taken in the plan's order (the order the sub-walk tree decides
 // variables in), so R0 is the R factor of Xc[:, order].
 #include <math.h>
@@ -17,6 +24,7 @@ constexpr int kPanelChunk = 64;  // rows staged in shared memory at a time
 constexpr int kLd = 33;          // row stride of the m x m shared-memory tiles
 constexpr int kRedThreads = 1024; // threads of the reduction kernels
 constexpr int kCholThreads = 1024;  // threads of the Cholesky kernel (one barrier per column)
+constexpr double kOnePassRatio = 1e-3;  // smallest RSS / sum of squares for one pass
 
 // All shared-memory tiles here are flat 1-D arrays indexed as [row * kLd + col]:
 // with this toolchain, runtime-indexed two-dimensional __shared__ arrays were
@@ -187,7 +195,9 @@ __device__ __forceinline__ void gram_sum_body(int g, const double* __restrict__ 
 __device__ __forceinline__ void chol_body(const double* __restrict__ gsum, int m,
                                           const double* __restrict__ R1, double* __restrict__ Rout,
                                           double* __restrict__ Rinv_out, int* __restrict__ status,
-                                          unsigned long long* chk) {
+                                          unsigned long long* chk,
+                                          double* __restrict__ R0_one = nullptr,
+                                          int* __restrict__ onepass = nullptr) {
     __shared__ double G[32 * kLd];
     __shared__ double R1s[32 * kLd];
     // pair table: pairs (a, b), a <= b, ordered by a, so that the pairs with
@@ -275,6 +285,18 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ gsum, int m
             if (GBN_IN(chk, 126, e, m * m)) Rinv_out[e] = (i <= c) ? B[i * kLd + c] : 0.0;
         }
     }
+    bool one = false;
+    if (!R1 && onepass) {  // is R1 accurate enough to be R0?  (see the top of this file)
+        bool ok = true;
+        if (tid < m) {
+            double cn2 = 0.0, ginv = 0.0;
+            for (int i = 0; i <= tid; ++i) cn2 = fma(G[i * kLd + tid], G[i * kLd + tid], cn2);
+            for (int j = tid; j < m; ++j) ginv = fma(R1s[tid * kLd + j], R1s[tid * kLd + j], ginv);
+            ok = cn2 > 0.0 && ginv > 0.0 && ginv * cn2 <= 1.0 / kOnePassRatio;
+        }
+        one = __syncthreads_and(ok) != 0;
+        if (one && tid == 0) *onepass = 1;
+    }
     __syncthreads();
     for (int e = tid; e < m * m; e += blockDim.x) {
         const int i = e / m, j = e % m;
@@ -286,7 +308,10 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ gsum, int m
                 v = G[i * kLd + j];
             }
         }
-        if (GBN_IN(chk, 125, e, m * m)) Rout[e] = v;
+        if (GBN_IN(chk, 125, e, m * m)) {
+            Rout[e] = v;
+            if (one) R0_one[e] = v;
+        }
     }
 }
 
@@ -294,6 +319,7 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ gsum, int m
 struct R0Ptrs {
     double *colsum, *mu, *gram, *gsum, *r1, *r1inv, *r0;
     int* status;
+    int* onepass;  // set by pass 1 when pass 2 is not needed
     unsigned long long* chk;
 };
 
@@ -307,6 +333,7 @@ __device__ __host__ __forceinline__ R0Ptrs r0_ptrs(const Plan& p, char* ws) {
     q.r1inv = reinterpret_cast<double*>(ws + p.off_r1inv);
     q.r0 = reinterpret_cast<double*>(ws + p.off_r0);
     q.status = reinterpret_cast<int*>(ws + p.off_status);
+    q.onepass = reinterpret_cast<int*>(ws + p.off_status + kR0OnePassOffset);
     q.chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
     return q;
 }
@@ -325,23 +352,26 @@ __global__ void __launch_bounds__(kRedThreads) mean_kernel(const Plan p, char* w
 __global__ void gram_kernel(const Plan p, const double* __restrict__ X, char* ws, int pass) {
     grid_dep_wait();
     const R0Ptrs q = r0_ptrs(p, ws);
+    if (pass && *q.onepass) return;
     gram_body(blockIdx.x, X, p.n, p.m, p.rows_per_panel, q.mu, p.panels, pass ? q.r1inv : nullptr,
               p, q.gram, q.chk);
 }
-__global__ void __launch_bounds__(kRedThreads) gram_sum_kernel(const Plan p, char* ws) {
+__global__ void __launch_bounds__(kRedThreads) gram_sum_kernel(const Plan p, char* ws, int pass) {
     grid_dep_wait();
     grid_dep_launch();
     const R0Ptrs q = r0_ptrs(p, ws);
+    if (pass && *q.onepass) return;
     gram_sum_body(blockIdx.x, q.gram, p.panels, p.m, q.gsum, q.chk);
 }
 __global__ void __launch_bounds__(kCholThreads) chol_kernel(const Plan p, char* ws, int pass) {
     grid_dep_wait();
     grid_dep_launch();
     const R0Ptrs q = r0_ptrs(p, ws);
-    if (pass)
-        chol_body(q.gsum, p.m, q.r1, q.r0, nullptr, q.status, q.chk);
-    else
-        chol_body(q.gsum, p.m, nullptr, q.r1, q.r1inv, q.status, q.chk);
+    if (pass) {
+        if (!*q.onepass) chol_body(q.gsum, p.m, q.r1, q.r0, nullptr, q.status, q.chk);
+    } else {
+        chol_body(q.gsum, p.m, nullptr, q.r1, q.r1inv, q.status, q.chk, q.r0, q.onepass);
+    }
 }
 
 // A batch: the position maps (block -> launch position) of panels (y = 0) and of
@@ -378,25 +408,28 @@ __global__ void gram_kernel_b(const BatchView v, int pass) {
     const int d = batch_locate(v, v.panel_prefix, v.panel_pos, blockIdx.x, local);
     const Plan& p = v.plans[d];
     const R0Ptrs q = r0_ptrs(p, v.ws[d]);
+    if (pass && *q.onepass) return;
     gram_body((int)local, v.X[d], p.n, p.m, p.rows_per_panel, q.mu, p.panels,
               pass ? q.r1inv : nullptr, p, q.gram, q.chk);
 }
 // grid (pair groups of the largest m, datasets)
-__global__ void __launch_bounds__(kRedThreads) gram_sum_kernel_b(const BatchView v) {
+__global__ void __launch_bounds__(kRedThreads) gram_sum_kernel_b(const BatchView v, int pass) {
     const int d = blockIdx.y;
     const Plan& p = v.plans[d];
     if ((int)blockIdx.x * 32 >= p.m * (p.m + 1) / 2) return;
     const R0Ptrs q = r0_ptrs(p, v.ws[d]);
+    if (pass && *q.onepass) return;
     gram_sum_body(blockIdx.x, q.gram, p.panels, p.m, q.gsum, q.chk);
 }
 __global__ void __launch_bounds__(kCholThreads) chol_kernel_b(const BatchView v, int pass) {
     const int d = blockIdx.x;
     const Plan& p = v.plans[d];
     const R0Ptrs q = r0_ptrs(p, v.ws[d]);
-    if (pass)
-        chol_body(q.gsum, p.m, q.r1, q.r0, nullptr, q.status, q.chk);
-    else
-        chol_body(q.gsum, p.m, nullptr, q.r1, q.r1inv, q.status, q.chk);
+    if (pass) {
+        if (!*q.onepass) chol_body(q.gsum, p.m, q.r1, q.r0, nullptr, q.status, q.chk);
+    } else {
+        chol_body(q.gsum, p.m, nullptr, q.r1, q.r1inv, q.status, q.chk, q.r0, q.onepass);
+    }
 }
 
 }  // namespace
@@ -410,10 +443,10 @@ int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream) {
     const cudaError_t e[] = {
         launch_dep(mean_kernel, dim3(1), dim3(kRedThreads), 0, stream, p, ws),
         launch_dep(gram_kernel, dim3(p.panels), dim3(512), 0, stream, p, X, ws, 0),
-        launch_dep(gram_sum_kernel, dim3(groups), dim3(kRedThreads), 0, stream, p, ws),
+        launch_dep(gram_sum_kernel, dim3(groups), dim3(kRedThreads), 0, stream, p, ws, 0),
         launch_dep(chol_kernel, dim3(1), dim3(kCholThreads), 0, stream, p, ws, 0),
         launch_dep(gram_kernel, dim3(p.panels), dim3(512), 0, stream, p, X, ws, 1),
-        launch_dep(gram_sum_kernel, dim3(groups), dim3(kRedThreads), 0, stream, p, ws),
+        launch_dep(gram_sum_kernel, dim3(groups), dim3(kRedThreads), 0, stream, p, ws, 1),
         launch_dep(chol_kernel, dim3(1), dim3(kCholThreads), 0, stream, p, ws, 1)};
     for (cudaError_t x : e)
         if (x != cudaSuccess) return GBN_ERR_CUDA;
@@ -429,10 +462,10 @@ int launch_r0_batched(const BatchView& v, int64_t total_panels, int max_m, cudaS
         launch_plain(colsum_kernel_b, dim3(P), dim3(256), 0, stream, v),
         launch_plain(mean_kernel_b, dim3(B), dim3(kRedThreads), 0, stream, v),
         launch_plain(gram_kernel_b, dim3(P), dim3(512), 0, stream, v, 0),
-        launch_plain(gram_sum_kernel_b, sum_grid, dim3(kRedThreads), 0, stream, v),
+        launch_plain(gram_sum_kernel_b, sum_grid, dim3(kRedThreads), 0, stream, v, 0),
         launch_plain(chol_kernel_b, dim3(B), dim3(kCholThreads), 0, stream, v, 0),
         launch_plain(gram_kernel_b, dim3(P), dim3(512), 0, stream, v, 1),
-        launch_plain(gram_sum_kernel_b, sum_grid, dim3(kRedThreads), 0, stream, v),
+        launch_plain(gram_sum_kernel_b, sum_grid, dim3(kRedThreads), 0, stream, v, 1),
         launch_plain(chol_kernel_b, dim3(B), dim3(kCholThreads), 0, stream, v, 1)};
     for (cudaError_t x : e)
         if (x != cudaSuccess) return GBN_ERR_CUDA;
