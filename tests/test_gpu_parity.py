@@ -281,3 +281,17 @@ def test_fp32_walk_forms_write_every_slot(m, q):
     assert not bool(torch.isnan(out).any()), "a slot was not written"
     _, ref = oracle.scores(X)
     _check(out.cpu().numpy(), ref, n, TOL[0])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("sigma", [0.06, 0.045, 0.02, 0.005])
+def test_r0_one_pass_boundary(precision, sigma):
+    """Column 3 = column 1 + sigma * noise, so its smallest RSS is about sigma^2 of its sum of
+    squares: above 1e-3 the R0 stage takes one Cholesky QR pass, below it two.  Either way
+    every score matches the oracle at the walk's tolerance."""
+    m, n = 10, 400
+    X = synthetic.sem_sample(m, n, 0.3, 9100)
+    X[:, 3] = X[:, 1] + sigma * np.std(X[:, 1]) * np.random.default_rng(3).standard_normal(n)
+    _, ref = oracle.scores(X)
+    got = _gpu(X, precision=precision, q=5)
+    _check(got.double().cpu().numpy(), ref, n, TOL[precision])
