@@ -121,8 +121,10 @@ typedef struct givensbn_opts {
  * runs over a factor of the posterior matrix t I + S_n (S_n the centred scatter matrix), so its
  * residuals are the Schur complements rho(c | S); a pass then forms ln det of every parent
  * block by the recursion L[S] = L[S - h] + ln rho(h | S - h) (h the highest variable of S) and
- * writes K(|S|) - ((n + alpha_w - m + |S| + 1) / 2) ln rho(c | S) - L[S] / 2.  Single-dataset
- * calls without shards only; the workspace grows by 2^m table elements. */
+ * writes K(|S|) - ((n + alpha_w - m + |S| + 1) / 2) ln rho(c | S) - L[S] / 2.  Higher is
+ * better (a log likelihood), unlike the other kinds: negate the table before
+ * givensbn_structure_search, which minimises.  Single-dataset calls without shards only; the
+ * workspace grows by 2^m table elements. */
 #define GBN_SCORE_BGE 3
 
 /* Default options: FP32, centring on, automatic q, no workspace, fixup_tau 1e-6, BIC score, no
