@@ -441,7 +441,10 @@ def _extras(dev, flush, args):
     out["batched"] = {"workload": "bootstrap_256 (m~U{12..20}, n~U{100..5000})", "datasets": len(Xs),
                       "families": total, "ms_per_batch": t, "value": total / (t / 1e3),
                       "unit": UNIT, "launch": "one captured CUDA graph",
-                      "q": q or None, "consumer_warps": cw or None, "autotune": tune}
+                      "q": q or None, "consumer_warps": cw or None, "autotune": tune,
+                      "hbm_floor_frac": 4 * total / (t / 1e3) / 1e9 / _peak_hbm()[0],
+                      "hbm_floor_note": "4 B per score written once, against the measured copy "
+                                        "bandwidth, over the whole batch call"}
     del tbl, ws, graph
     Gs, w = synthetic.gradient_workload()
     Gd = [torch.from_numpy(X).to(dev) for X in Gs]

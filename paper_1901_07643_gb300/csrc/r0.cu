@@ -20,7 +20,7 @@
 namespace gbn {
 namespace {
 
-constexpr int kPanelChunk = 64;  // rows staged in shared memory at a time
+constexpr int kPanelChunk = 32;  // rows staged in shared memory at a time (even: see gram_body)
 constexpr int kLd = 33;          // row stride of the m x m shared-memory tiles
 constexpr int kRedThreads = 1024; // threads of the reduction kernels
 constexpr int kCholThreads = 1024;  // threads of the Cholesky kernel (one barrier per column)
@@ -81,7 +81,10 @@ __device__ __forceinline__ void mean_body(const double* __restrict__ colsum, int
 
 // Partial Gram of one row panel: sum over its rows of y y^T (upper triangle,
 // packed by pairs i <= j), where y is the centred row in plan order, or for
-// pass 2 the row of Q1 = y R1^{-1} (Rinv = R1^{-1}, upper triangular).
+// pass 2 the row of Q1 = y R1^{-1} (Rinv = R1^{-1}, upper triangular).  Each
+// pair's thread adds the panel's even rows into one sum and the odd rows into
+// another (rows staged kPanelChunk at a time; the chunk size is even, so the
+// split, and the result, do not depend on it).
 __device__ __forceinline__ void gram_body(int blk, const double* __restrict__ X, int64_t n, int m,
                                           int rows_per, const double* __restrict__ mu_g, int panels,
                                           const double* __restrict__ Rinv, const Plan& plan,
@@ -338,6 +341,11 @@ __device__ __host__ __forceinline__ R0Ptrs r0_ptrs(const Plan& p, char* ws) {
     return q;
 }
 
+// Threads of a Gram block: one per column pair (i <= j), in whole warps of 256
+// or 512.  The smaller block leaves fewer idle warps at the panel's barriers and
+// fits twice as many blocks on an SM; a pair's sum does not depend on it.
+inline unsigned gram_threads(int m) { return m * (m + 1) / 2 <= 256 ? 256u : 512u; }
+
 // One dataset: the plan travels as a kernel parameter.
 __global__ void colsum_kernel(const Plan p, const double* __restrict__ X, char* ws) {
     const R0Ptrs q = r0_ptrs(p, ws);
@@ -442,10 +450,10 @@ int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream) {
     const unsigned groups = (unsigned)((p.m * (p.m + 1) / 2 + 31) / 32);
     const cudaError_t e[] = {
         launch_dep(mean_kernel, dim3(1), dim3(kRedThreads), 0, stream, p, ws),
-        launch_dep(gram_kernel, dim3(p.panels), dim3(512), 0, stream, p, X, ws, 0),
+        launch_dep(gram_kernel, dim3(p.panels), dim3(gram_threads(p.m)), 0, stream, p, X, ws, 0),
         launch_dep(gram_sum_kernel, dim3(groups), dim3(kRedThreads), 0, stream, p, ws, 0),
         launch_dep(chol_kernel, dim3(1), dim3(kCholThreads), 0, stream, p, ws, 0),
-        launch_dep(gram_kernel, dim3(p.panels), dim3(512), 0, stream, p, X, ws, 1),
+        launch_dep(gram_kernel, dim3(p.panels), dim3(gram_threads(p.m)), 0, stream, p, X, ws, 1),
         launch_dep(gram_sum_kernel, dim3(groups), dim3(kRedThreads), 0, stream, p, ws, 1),
         launch_dep(chol_kernel, dim3(1), dim3(kCholThreads), 0, stream, p, ws, 1)};
     for (cudaError_t x : e)
@@ -461,10 +469,10 @@ int launch_r0_batched(const BatchView& v, int64_t total_panels, int max_m, cudaS
         launch_plain(status_clear_kernel_b, dim3(B), dim3(64), 0, stream, v),
         launch_plain(colsum_kernel_b, dim3(P), dim3(256), 0, stream, v),
         launch_plain(mean_kernel_b, dim3(B), dim3(kRedThreads), 0, stream, v),
-        launch_plain(gram_kernel_b, dim3(P), dim3(512), 0, stream, v, 0),
+        launch_plain(gram_kernel_b, dim3(P), dim3(gram_threads(max_m)), 0, stream, v, 0),
         launch_plain(gram_sum_kernel_b, sum_grid, dim3(kRedThreads), 0, stream, v, 0),
         launch_plain(chol_kernel_b, dim3(B), dim3(kCholThreads), 0, stream, v, 0),
-        launch_plain(gram_kernel_b, dim3(P), dim3(512), 0, stream, v, 1),
+        launch_plain(gram_kernel_b, dim3(P), dim3(gram_threads(max_m)), 0, stream, v, 1),
         launch_plain(gram_sum_kernel_b, sum_grid, dim3(kRedThreads), 0, stream, v, 1),
         launch_plain(chol_kernel_b, dim3(B), dim3(kCholThreads), 0, stream, v, 1)};
     for (cudaError_t x : e)
