@@ -23,6 +23,7 @@ namespace {
 constexpr int kPanelChunk = 32;  // rows staged in shared memory at a time (even: see gram_body)
 constexpr int kLd = 33;          // row stride of the m x m shared-memory tiles
 constexpr int kRedThreads = 1024; // threads of the reduction kernels
+constexpr int kColsumThreads = 128;  // threads of a column-sum block (16 blocks per SM)
 constexpr int kCholThreads = 1024;  // threads of the Cholesky kernel (one barrier per column)
 constexpr double kOnePassRatio = 1e-3;  // smallest RSS / sum of squares for one pass
 
@@ -445,7 +446,8 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel_b(const BatchView v,
 int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream) {
     if (cudaMemsetAsync(ws + p.off_status, 0, 256, stream) != cudaSuccess) return GBN_ERR_CUDA;
     if (p.center &&
-        launch_plain(colsum_kernel, dim3(p.panels), dim3(256), 0, stream, p, X, ws) != cudaSuccess)
+        launch_plain(colsum_kernel, dim3(p.panels), dim3(kColsumThreads), 0, stream, p, X, ws) !=
+            cudaSuccess)
         return GBN_ERR_CUDA;
     const unsigned groups = (unsigned)((p.m * (p.m + 1) / 2 + 31) / 32);
     const cudaError_t e[] = {
@@ -467,7 +469,7 @@ int launch_r0_batched(const BatchView& v, int64_t total_panels, int max_m, cudaS
     const cudaError_t e[] = {
         launch_plain(batch_pos_kernel, dim3(B, 2), dim3(256), 0, stream, v),
         launch_plain(status_clear_kernel_b, dim3(B), dim3(64), 0, stream, v),
-        launch_plain(colsum_kernel_b, dim3(P), dim3(256), 0, stream, v),
+        launch_plain(colsum_kernel_b, dim3(P), dim3(kColsumThreads), 0, stream, v),
         launch_plain(mean_kernel_b, dim3(B), dim3(kRedThreads), 0, stream, v),
         launch_plain(gram_kernel_b, dim3(P), dim3(gram_threads(max_m)), 0, stream, v, 0),
         launch_plain(gram_sum_kernel_b, sum_grid, dim3(kRedThreads), 0, stream, v, 0),
