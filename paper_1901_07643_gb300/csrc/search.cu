@@ -89,6 +89,167 @@ __global__ void __launch_bounds__(kTileThreads)
     }
 }
 
+// The same passes with the levels spread over registers, lanes and warps, so
+// that most of them need no barrier; the levels still run in ascending bit order
+// with the subset winning ties, so every minimum and argmin equals
+// tile_transform's.
+//
+// First pass, 12 bits: a tile is 4096 consecutive entries of a child block;
+// thread t holds entries t + 512 k (k < 8): mask bits 0-4 are its lane (levels
+// by shuffles), 5-8 its warp (through shared memory, one barrier per level), 9-11
+// its register index.
+__global__ void __launch_bounds__(kTileThreads)
+    bps_first12_kernel(const float* __restrict__ src, float* __restrict__ best,
+                       uint32_t* __restrict__ bset, int m) {
+    __shared__ float sv[4096];
+    __shared__ uint32_t ss[4096];
+    const int t = threadIdx.x, lane = t & 31;
+    const int64_t block = (int64_t)1 << (m - 1);
+    const int64_t tiles_per_child = block >> 12;
+    const int64_t child = blockIdx.x / tiles_per_child;
+    const int64_t r = blockIdx.x % tiles_per_child;
+    const int64_t base = child * block + (r << 12);
+    float v[8];
+    uint32_t s[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        v[k] = src[base + t + 512 * k];
+        s[k] = (uint32_t)((r << 12) + t + 512 * k);  // the compressed mask itself
+    }
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+        const bool hi = (lane >> b) & 1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float a = __shfl_xor_sync(0xffffffffu, v[k], 1 << b);
+            const uint32_t sa = __shfl_xor_sync(0xffffffffu, s[k], 1 << b);
+            if (hi && a <= v[k]) {
+                v[k] = a;
+                s[k] = sa;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        sv[t + 512 * k] = v[k];
+        ss[t + 512 * k] = s[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 5; b < 9; ++b) {  // reads are of entries with bit b clear, writes with it set
+        if ((t >> b) & 1) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int lo = (t + 512 * k) ^ (1 << b);
+                const float a = sv[lo];
+                if (a <= v[k]) {
+                    v[k] = a;
+                    s[k] = ss[lo];
+                    sv[t + 512 * k] = a;
+                    ss[t + 512 * k] = s[k];
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if ((k >> b) & 1) {
+                const int lo = k ^ (1 << b);
+                if (v[lo] <= v[k]) {
+                    v[k] = v[lo];
+                    s[k] = s[lo];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        best[base + t + 512 * k] = v[k];
+        bset[base + t + 512 * k] = s[k];
+    }
+}
+
+// A later pass over rbits (4..7) bits from b0: a tile is 2^rbits rows (stride
+// 2^b0) of kCols consecutive entries; lane = column, warp w holds rows w + 16 j
+// (j < 2^(rbits-4)): row bits 0-3 are the warp (through shared memory), the rest
+// registers.
+__global__ void __launch_bounds__(kTileThreads)
+    bps_strided_kernel(float* __restrict__ best, uint32_t* __restrict__ bset, int m, int b0,
+                       int rbits) {
+    __shared__ float sv[128 * kCols];
+    __shared__ uint32_t ss[128 * kCols];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int nr = 1 << (rbits - 4);  // rows per thread
+    const int rows = 1 << rbits;
+    const int64_t block = (int64_t)1 << (m - 1);
+    const int64_t groups_lo = ((int64_t)1 << b0) / kCols;
+    const int64_t tiles_per_child = block / ((int64_t)rows * kCols);
+    const int64_t child = blockIdx.x / tiles_per_child;
+    const int64_t r = blockIdx.x % tiles_per_child;
+    const int64_t lo_g = r % groups_lo, hi_g = r / groups_lo;
+    const int64_t base = child * block + (hi_g << (b0 + rbits)) + lo_g * kCols + lane;
+    float v[8];
+    uint32_t s[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j < nr) {
+            const int64_t idx = base + ((int64_t)(w + 16 * j) << b0);
+            v[j] = best[idx];
+            s[j] = bset[idx];
+            sv[(w + 16 * j) * kCols + lane] = v[j];
+            ss[(w + 16 * j) * kCols + lane] = s[j];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {  // reads are of rows with bit b clear, writes with it set
+        if ((w >> b) & 1) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (j < nr) {
+                    const int row = w + 16 * j;
+                    const int lo = (row ^ (1 << b)) * kCols + lane;
+                    const float a = sv[lo];
+                    if (a <= v[j]) {
+                        v[j] = a;
+                        s[j] = ss[lo];
+                        sv[row * kCols + lane] = a;
+                        ss[row * kCols + lane] = s[j];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        if (b < rbits - 4) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (j < nr && ((j >> b) & 1)) {
+                    const int lo = j ^ (1 << b);
+                    if (v[lo] <= v[j]) {
+                        v[j] = v[lo];
+                        s[j] = s[lo];
+                    }
+                }
+            }
+        }
+    }
+    (void)rows;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j < nr) {
+            const int64_t idx = base + ((int64_t)(w + 16 * j) << b0);
+            best[idx] = v[j];
+            bset[idx] = s[j];
+        }
+    }
+}
+
 // The rank-th p-subset of {0..m-1} (combinatorial number system, largest
 // element first) as a bitmask; binom[x * 33 + k] = C(x, k).
 __device__ __forceinline__ uint32_t unrank(long long rank, int p, int m, const long long* binom) {
@@ -193,13 +354,23 @@ int run_bps(const float* scores, int m, float* best, uint32_t* bset, cudaStream_
             C = kCols;
         }
         const int64_t tiles = table / ((int64_t)C << rb);
-        const size_t smem = (size_t)(8 << rb) * C;
-        if (cudaFuncSetAttribute(bps_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
-            return GBN_ERR_CUDA;
-        if (launch_plain(bps_pass_kernel, dim3((unsigned)tiles), dim3(kTileThreads), smem, stream,
-                         scores, best, bset, m, b0, rb, first ? 1 : 0) != cudaSuccess)
-            return GBN_ERR_CUDA;
+        if (first && rb == kFirstBits) {
+            if (launch_plain(bps_first12_kernel, dim3((unsigned)tiles), dim3(kTileThreads), 0,
+                             stream, scores, best, bset, m) != cudaSuccess)
+                return GBN_ERR_CUDA;
+        } else if (!first && rb >= 4) {
+            if (launch_plain(bps_strided_kernel, dim3((unsigned)tiles), dim3(kTileThreads), 0,
+                             stream, best, bset, m, b0, rb) != cudaSuccess)
+                return GBN_ERR_CUDA;
+        } else {  // small tables and short last passes
+            const size_t smem = (size_t)(8 << rb) * C;
+            if (cudaFuncSetAttribute(bps_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return GBN_ERR_CUDA;
+            if (launch_plain(bps_pass_kernel, dim3((unsigned)tiles), dim3(kTileThreads), smem,
+                             stream, scores, best, bset, m, b0, rb, first ? 1 : 0) != cudaSuccess)
+                return GBN_ERR_CUDA;
+        }
         b0 += rb;
         first = false;
     }
