@@ -202,47 +202,8 @@ __device__ __forceinline__ float wk_log2(float x) {
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// FP64: a table-driven base-2 logarithm after Tang ("Table-driven implementation
-// of the logarithm function in IEEE floating-point arithmetic", ACM TOMS 16(4),
-// 1990).  x = 2^k m with m in [1, 2); F = 1 + j/128 is the 128th nearest to m,
-// so u = m/F - 1 has |u| <= 2^-8 (one FMA with the tabulated 1/F: its rounding
-// moves u by 2^-53 absolute); then
-//     log2 x = k + log2 F + log(1 + u) / ln 2,
-// log(1 + u) by its Taylor series through u^6 (the next term is below 2^-58).
-// The block's table (log2 F, 1/F for j = 0..128) sits in shared memory, filled at
-// the start of each FP64 walk block from the library's log2.  Zero, infinity and
-// NaN take log2 itself.
-constexpr int kLogTab = 129;
-__shared__ double s_log2_tab[2 * kLogTab];
-
-__device__ __forceinline__ void log2_table_init() {
-    for (int j = threadIdx.x; j < kLogTab; j += blockDim.x) {
-        const double F = 1.0 + (double)j * 0.0078125;
-        s_log2_tab[2 * j] = log2(F);
-        s_log2_tab[2 * j + 1] = 1.0 / F;
-    }
-}
-
-__device__ __forceinline__ double wk_log2(double x) {
-    if (!(x > 0.0 && x < __longlong_as_double(0x7FF0000000000000ll))) return log2(x);
-    long long b = __double_as_longlong(x);
-    int k = 0;
-    if ((b >> 52) == 0) {  // subnormal: scale into the normal range first
-        b = __double_as_longlong(x * 0x1p54);
-        k = -54;
-    }
-    k += (int)(b >> 52) - 1023;
-    const long long fr = b & 0x000FFFFFFFFFFFFFll;
-    const int j = (int)((fr + (1ll << 44)) >> 45);  // 0 .. 128
-    const double mm = __longlong_as_double(fr | 0x3FF0000000000000ll);
-    const double u = fma(mm, s_log2_tab[2 * j + 1], -1.0);
-    double p = fma(u, -1.0 / 6.0, 0.2);
-    p = fma(p, u, -0.25);
-    p = fma(p, u, 1.0 / 3.0);
-    p = fma(p, u, -0.5);
-    const double l1p = fma(p, u * u, u);  // log(1 + u)
-    return (double)k + fma(l1p, 1.4426950408889634, s_log2_tab[2 * j]);
-}
+// FP64: the library's base-2 logarithm.
+__device__ __forceinline__ double wk_log2(double x) { return log2(x); }
 __device__ __forceinline__ float2 wk_pair(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 wk_pair(double a, double b) { return make_double2(a, b); }
 
@@ -1092,7 +1053,6 @@ __device__ __forceinline__ void walk_body(const WalkArgs<T>& a, uint64_t cta) {
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::off_bar);
     if (threadIdx.x < S::chunks) mbar_init(&full[threadIdx.x], 1);
     for (int c = threadIdx.x + blockDim.x; c < S::chunks; c += blockDim.x) mbar_init(&full[c], 1);
-    if constexpr (std::is_same<T, double>::value) log2_table_init();
     __syncthreads();
     // cta: this launch's CTA (leaf record); g: its global index (front set bits)
     const uint64_t g = cta + (uint64_t)a.cta0;
