@@ -382,7 +382,7 @@ def _e2e(X, Xd, fam, q32, cw32, w, world, dev, args):
     best = min(res, key=res.get)
     # the host link alone: the same table, device -> pinned host, one copy, nothing else
     cp = []
-    for _ in range(3):
+    for _ in range(5):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         outh.copy_(outd, non_blocking=True)
@@ -390,7 +390,7 @@ def _e2e(X, Xd, fam, q32, cw32, w, world, dev, args):
         torch.cuda.synchronize()
         cp.append(a.elapsed_time(b))
     d2h = int(outh.numel() * outh.element_size())
-    copy_ms = statistics.median(cp)
+    copy_ms = min(cp)
     return {"value": world * fam / (res[best] / 1e3), "unit": UNIT,
             "h2d_bytes_per_step": int(Xh.numel() * Xh.element_size()),
             "d2h_bytes_per_step": d2h,
@@ -398,7 +398,7 @@ def _e2e(X, Xd, fam, q32, cw32, w, world, dev, args):
             "ms_per_step_by_method": res,
             "host_link": {"d2h_copy_ms": copy_ms, "d2h_gbs": d2h / (copy_ms / 1e3) / 1e9,
                           "how": "one cudaMemcpyAsync of the table, device to pinned host "
-                                 "(median of 3, CUDA events)"},
+                                 "(best of 5, CUDA events)"},
             "note": "value is the fastest of the three delivery methods listed"}
 
 
