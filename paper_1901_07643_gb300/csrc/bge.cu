@@ -122,6 +122,10 @@ __global__ void __launch_bounds__(256) bge_logdet_kernel(const Plan p, const T* 
 __device__ __forceinline__ uint64_t parent_set(int c, uint64_t cm) {
     return (cm & ((1ull << c) - 1ull)) | ((cm >> c) << (c + 1));
 }
+// The compressed mask of set S for child c (S without c): bit c removed.
+__device__ __forceinline__ uint64_t parent_set_inv(int c, uint64_t S) {
+    return (S & ((1ull << c) - 1ull)) | ((S >> (c + 1)) << c);
+}
 
 template <typename T>
 __device__ __forceinline__ T bge_value(T v, T Ls, int l, const T* K, const T* a, T inv_n, T ln_n) {
@@ -187,6 +191,67 @@ __global__ void __launch_bounds__(256) bge_finalize_kernel(const Plan p, T* __re
     }
 }
 
+// FP32 with m >= 13: one block per block of 4096 variable sets S = H | low (H the
+// sets' bits from 12 up, low < 4096): their L values are read once into shared
+// memory, then every child's slots for these sets are rewritten.  For a child
+// c >= 12 outside H the 4096 slots are contiguous (compress keeps the low 12
+// bits); for c < 12 the 2048 sets without c are, at c 2^(m-1) + H/2 + j with
+// low the 12-bit value j spread around bit c.  So L is read once (2^m elements)
+// instead of once per child.
+__global__ void __launch_bounds__(256) bge_finalize_sets_kernel(const Plan p,
+                                                                float* __restrict__ table,
+                                                                const float* __restrict__ L,
+                                                                const BgeCoef co) {
+    __shared__ float Ls[4096];
+    __shared__ float K[32], a[32];
+    if (threadIdx.x < 32) {
+        K[threadIdx.x] = (float)co.K[threadIdx.x];
+        a[threadIdx.x] = (float)co.a[threadIdx.x];
+    }
+    grid_dep_wait();
+    const uint64_t H = (uint64_t)blockIdx.x << 12;
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x)
+        reinterpret_cast<float4*>(Ls)[i] = reinterpret_cast<const float4*>(L + H)[i];
+    __syncthreads();
+    const int m = p.m;
+    const int64_t half = (int64_t)1 << (m - 1);
+    const float inv_n = (float)co.inv_n, ln_n = (float)co.ln_n;
+    const int hp = __popcll(H);
+    for (int c = 0; c < m; ++c) {
+        if (c >= 12) {
+            if ((H >> c) & 1ull) continue;  // every set of the block holds c
+            float4* t4 = reinterpret_cast<float4*>(table + (int64_t)c * half +
+                                                   (int64_t)parent_set_inv(c, H));
+            for (int q = threadIdx.x; q < 1024; q += blockDim.x) {
+                float4 v = t4[q];
+                float* vv = reinterpret_cast<float*>(&v);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int low = 4 * q + i;
+                    const int l = hp + __popc(low);
+                    if (l <= p.kmax) vv[i] = bge_value(vv[i], Ls[low], l, K, a, inv_n, ln_n);
+                }
+                t4[q] = v;
+            }
+        } else {
+            float4* t4 = reinterpret_cast<float4*>(table + (int64_t)c * half + (int64_t)(H >> 1));
+            const unsigned below = (1u << c) - 1u;
+            for (int q = threadIdx.x; q < 512; q += blockDim.x) {
+                float4 v = t4[q];
+                float* vv = reinterpret_cast<float*>(&v);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const unsigned j = 4u * q + i;
+                    const unsigned low = (j & below) | ((j & ~below) << 1);
+                    const int l = hp + __popc(low);
+                    if (l <= p.kmax) vv[i] = bge_value(vv[i], Ls[low], l, K, a, inv_n, ln_n);
+                }
+                t4[q] = v;
+            }
+        }
+    }
+}
+
 template <typename T>
 int launch_finalize_t(const Plan& p, char* ws, T* out, cudaStream_t stream) {
     T* L = reinterpret_cast<T*>(ws + p.off_bge);
@@ -217,6 +282,11 @@ int launch_finalize_t(const Plan& p, char* ws, T* out, cudaStream_t stream) {
         if (launch_dep(bge_logdet_kernel<T>, dim3(nb), dim3(256), 0, stream, p, (const T*)out, L,
                        h, co) != cudaSuccess)
             return GBN_ERR_CUDA;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (m >= 13)
+            return launch_rc(launch_dep(bge_finalize_sets_kernel, dim3((unsigned)(1u << (m - 12))),
+                                        dim3(256), 0, stream, p, (float*)out, (const float*)L, co));
     }
     const int64_t total = (int64_t)m << (m - 1);
     const int64_t want = (total / 4 + 255) / 256 + 1;
