@@ -510,8 +510,13 @@ def _bge_leg(Xd, w, flush, slots_t, gathered):
         gathered["bge"] = out[slots_t[:4096]].double().cpu().numpy()
     t = statistics.median(ms)
     del out, ws
+    # algorithmic HBM bytes of the whole call: the walk writes the table, the log-determinant
+    # recursion reads one block per level and writes L (2^m sets), the rewrite pass reads and
+    # writes the table and reads L once
+    algo = 4 * fam + 8 * fam + 4 * 3 * (1 << w.m) + 4 * (1 << w.m)
     return {"workload": f"{w.name}, BGe score (alpha_mu 1, alpha_w m + 2)", "ms": t,
-            "value": fam / (t / 1e3), "unit": UNIT}
+            "value": fam / (t / 1e3), "unit": UNIT,
+            "hbm_frac": algo / (t / 1e3) / 1e9 / _peak_hbm()[0], "algorithmic_bytes": algo}
 
 
 def _search_leg(table, m, flush, args):
