@@ -378,7 +378,7 @@ int givensbn_family_coefficients(const double* X, int64_t n, int32_t m, const in
  *   total     device, one double: the optimal network score (the FP64 sum of the chosen
  *             table entries)
  *   opts      host; workspace >= givensbn_structure_search_workspace_size(m) (8 bytes per
- *             table slot plus 9 bytes per variable subset; 7.3 GB at m = 26)
+ *             table slot plus 9 bytes per variable subset and 8.4 KB; 7.3 GB at m = 26)
  * Both are asynchronous on opts->stream and return 0 or GBN_ERR_*.
  */
 int givensbn_best_parents(const float* scores, int32_t m, float* best, uint32_t* best_set,

@@ -269,15 +269,25 @@ __device__ __forceinline__ uint32_t compress_mask(uint32_t U, int c) {
 }
 
 // Subsets W of size p: F[W] and its sink.
-__global__ void dp_layer_kernel(const float* __restrict__ best, double* __restrict__ F,
-                                uint8_t* __restrict__ sink, int m, int p, long long count) {
-    __shared__ long long binom[32 * 33];
-    for (int e = threadIdx.x; e < m * 33; e += blockDim.x) {  // C(x, k), x < m, k <= 32
-        const int x = e / 33, k = e % 33;
-        long long c = k <= x ? 1 : 0;
-        for (int i = 1; i <= k && i <= x; ++i) c = c * (x - k + i) / i;  // exact at every step
-        binom[e] = c;
+// C(x, k) for x < 32, k <= 32 by Pascal's rule (additions only, exact), once per
+// search, into g[x * 33 + k]; one block of 33 threads, thread = k.
+__global__ void binom_kernel(long long* __restrict__ g) {
+    __shared__ long long row[2][33];
+    const int k = threadIdx.x;
+    for (int x = 0; x < 32; ++x) {
+        const long long* prev = row[(x + 1) & 1];
+        const long long v = k == 0 ? 1 : (x == 0 ? 0 : prev[k - 1] + prev[k]);
+        row[x & 1][k] = v;
+        g[x * 33 + k] = v;
+        __syncthreads();
     }
+}
+
+__global__ void dp_layer_kernel(const float* __restrict__ best, double* __restrict__ F,
+                                uint8_t* __restrict__ sink, int m, int p, long long count,
+                                const long long* __restrict__ gbinom) {
+    __shared__ long long binom[32 * 33];
+    for (int e = threadIdx.x; e < m * 33; e += blockDim.x) binom[e] = gbinom[e];  // C(x, k)
     __syncthreads();
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= count) return;
@@ -319,7 +329,7 @@ __global__ void backtrack_kernel(const double* __restrict__ F, const uint8_t* __
 }
 
 struct SearchLayout {
-    size_t off_best = 0, off_set = 0, off_F = 0, off_sink = 0, total = 0;
+    size_t off_best = 0, off_set = 0, off_F = 0, off_sink = 0, off_binom = 0, total = 0;
 };
 
 SearchLayout search_layout(int m) {
@@ -335,6 +345,8 @@ SearchLayout search_layout(int m) {
     off = up(off + sizeof(double) * ((size_t)1 << m));
     L.off_sink = off;
     off = up(off + ((size_t)1 << m));
+    L.off_binom = off;
+    off = up(off + sizeof(long long) * 32 * 33);
     L.total = off;
     return L;
 }
@@ -418,14 +430,17 @@ extern "C" int givensbn_structure_search(const float* scores, int32_t m, uint32_
     double* F = reinterpret_cast<double*>(ws + L.off_F);
     uint8_t* sink = reinterpret_cast<uint8_t*>(ws + L.off_sink);
     if ((rc = run_bps(scores, m, best, bset, stream))) return rc;
-    if (launch_plain(dp_init_kernel, dim3(1), dim3(1), 0, stream, F) != cudaSuccess)
+    long long* gbinom = reinterpret_cast<long long*>(ws + L.off_binom);
+    if (launch_plain(dp_init_kernel, dim3(1), dim3(1), 0, stream, F) != cudaSuccess ||
+        launch_plain(binom_kernel, dim3(1), dim3(33), 0, stream, gbinom) != cudaSuccess)
         return GBN_ERR_CUDA;
     long long cnt = 1;  // C(m, p)
     for (int p = 1; p <= m; ++p) {
         cnt = cnt * (m - p + 1) / p;
         const unsigned blocks = (unsigned)((cnt + 255) / 256);
         if (launch_plain(dp_layer_kernel, dim3(blocks), dim3(256), 0, stream,
-                         (const float*)best, F, sink, (int)m, p, cnt) != cudaSuccess)
+                         (const float*)best, F, sink, (int)m, p, cnt,
+                         (const long long*)gbinom) != cudaSuccess)
             return GBN_ERR_CUDA;
     }
     return launch_rc(launch_plain(backtrack_kernel, dim3(1), dim3(1), 0, stream, (const double*)F,
