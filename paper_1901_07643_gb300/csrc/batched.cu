@@ -255,7 +255,12 @@ extern "C" int score_all_families_batched(const double* const* Xs, const int64_t
     int max_m = 1;
     for (int b = 0; b < B; ++b) max_m = std::max(max_m, L.plans[b].m);
     if ((rc = launch_r0_batched(v, L.total_panels, max_m, stream))) return rc;
-    if ((rc = launch_roots_batched(v, L.total_cta, L.Q, L.maxW, L.max_stride, precision, stream))) return rc;
+    int64_t dfs_cta = 0;  // the launch-order prefix of datasets with at least 4 walk CTAs
+    for (int i = 0; i < B && L.plans[L.launch_order[i]].n_cta >= 4; ++i)
+        dfs_cta += L.plans[L.launch_order[i]].n_cta;
+    if ((rc = launch_roots_batched(v, L.total_cta, dfs_cta, L.Q, L.maxW, L.max_stride, precision,
+                                   stream)))
+        return rc;
     return launch_walk_batched(v, L.total_cta, L.Q, precision, opts->debug_coverage != 0,
                                L.n_cwarps, stream);
 }

@@ -261,7 +261,9 @@ BwdArgs bwd_args(const Plan& p, char* ws, const double* X, const void* w, double
 int launch_bwd_batched(const BwdArgs* args, const int64_t* prefix, int B, int B_narrow,
                        int64_t warps_narrow, int64_t warps_wide, int precision,
                        cudaStream_t stream);
-int launch_roots_batched(const BatchView& v, int64_t total_cta, int Q, int max_w,
+// dfs_cta: the walk CTAs of the launch-order prefix of datasets with at least 4
+// CTAs each (their top nodes depth first, four CTAs per warp).
+int launch_roots_batched(const BatchView& v, int64_t total_cta, int64_t dfs_cta, int Q, int max_w,
                          size_t max_stride, int precision, cudaStream_t stream);
 int launch_walk_batched(const BatchView& v, int64_t total_cta, int Q, int precision, bool coverage,
                         int n_cwarps, cudaStream_t stream);

@@ -709,12 +709,14 @@ __global__ void __launch_bounds__(32 * kDfsWarps, (std::is_same<T, float>::value
         leaves_body<T>(top_nodes<T>(p, ws), p, leaves, chk, cta, stack);
 }
 
-// A batch: warps find their dataset through the prefix of walk CTAs.
+// A batch: warps find their dataset through the prefix of walk CTAs.  Warp w
+// follows the path of global CTA c0 + w (c0: the first CTA of the datasets too
+// small for the depth-first form below).
 template <typename T>
-__global__ void __launch_bounds__(32 * kTopWarps) roots_top_kernel_b(const BatchView v) {
+__global__ void __launch_bounds__(32 * kTopWarps) roots_top_kernel_b(const BatchView v, int64_t c0) {
     __shared__ T S[kTopWarps * 32 * 32];
     const int warp = threadIdx.x >> 5;
-    const int64_t g = (int64_t)blockIdx.x * kTopWarps + warp;
+    const int64_t g = c0 + (int64_t)blockIdx.x * kTopWarps + warp;
     if (g >= v.cta_prefix[v.B]) return;
     int64_t local;
     const int d = batch_locate(v, v.cta_prefix, v.cta_pos, g, local);
@@ -840,20 +842,56 @@ int launch_leaves_bq(const BatchView& v, int64_t total_cta, size_t max_stride,
                                   smem, stream, v, max_stride));
 }
 
+// A batch, the datasets with at least 4 walk CTAs (a prefix of the launch order,
+// which is largest first, so every such dataset's first CTA is a multiple of 4):
+// warp w takes the depth-first group w - (that dataset's first CTA) / 4 of the
+// dataset, as the single-dataset kernel does, so the nodes are the same.
+constexpr int kTopDfsStackMax = 2 * 32 * 32;  // two saved levels of at most 32 rows
 template <typename T>
-int launch_roots_batched_t(const BatchView& v, int64_t total_cta, int Q, int max_w,
-                           size_t max_stride, cudaStream_t stream) {
+__global__ void __launch_bounds__(32 * kTopDfsWarps) roots_top_dfs_kernel_b(const BatchView v,
+                                                                            int64_t n_warps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * kTopDfsWarps + warp;
+    if (gw >= n_warps) return;
+    int64_t local;
+    const int d = batch_locate(v, v.cta_prefix, v.cta_pos, 4 * gw, local);
+    const Plan& p = v.plans[d];
+    char* ws = v.ws[d];
+    T* base = reinterpret_cast<T*>(smem_raw) + (size_t)warp * (32 * 32 + kTopDfsStackMax);
+    top_dfs_body<T>(reinterpret_cast<const double*>(ws + p.off_r0), p, top_nodes<T>(p, ws),
+                    reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset),
+                    (uint64_t)(local >> 2), base, base + 32 * 32);
+}
+
+template <typename T>
+int launch_roots_batched_t(const BatchView& v, int64_t total_cta, int64_t dfs_cta, int Q,
+                           int max_w, size_t max_stride, cudaStream_t stream) {
     if (Q + max_w > kDfsRows) return GBN_ERR_Q;
     const size_t smem = sizeof(T) * warp_smem_elems(Q, max_w, max_stride) * kDfsWarps;
     if (smem > 227 * 1024) return GBN_ERR_Q;
     if (cudaFuncSetAttribute(roots_leaves_kernel_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return GBN_ERR_CUDA;
-    const unsigned nb_top = (unsigned)((total_cta + kTopWarps - 1) / kTopWarps);
     const unsigned nb_dfs = (unsigned)((total_cta + kDfsWarps - 1) / kDfsWarps);
-    if (launch_plain(roots_top_kernel_b<T>, dim3(nb_top), dim3(32 * kTopWarps), 0, stream, v) !=
-        cudaSuccess)
-        return GBN_ERR_CUDA;
+    if (dfs_cta > 0) {  // top nodes of the larger datasets, depth first
+        const int64_t n_warps = dfs_cta / 4;
+        const size_t smem_top = sizeof(T) * (32 * 32 + kTopDfsStackMax) * kTopDfsWarps;
+        if (cudaFuncSetAttribute(roots_top_dfs_kernel_b<T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_top) != cudaSuccess)
+            return GBN_ERR_CUDA;
+        const unsigned nb = (unsigned)((n_warps + kTopDfsWarps - 1) / kTopDfsWarps);
+        if (launch_plain(roots_top_dfs_kernel_b<T>, dim3(nb), dim3(32 * kTopDfsWarps), smem_top,
+                         stream, v, n_warps) != cudaSuccess)
+            return GBN_ERR_CUDA;
+    }
+    if (total_cta > dfs_cta) {  // the rest, one path per CTA
+        const unsigned nb_top = (unsigned)((total_cta - dfs_cta + kTopWarps - 1) / kTopWarps);
+        if (launch_plain(roots_top_kernel_b<T>, dim3(nb_top), dim3(32 * kTopWarps), 0, stream, v,
+                         dfs_cta) != cudaSuccess)
+            return GBN_ERR_CUDA;
+    }
     bool reg = false;
     if constexpr (std::is_same<T, float>::value) reg = v.pairs && leaves_in_registers<T>(Q, 5);
     if (reg) {
@@ -886,10 +924,12 @@ int launch_roots(const Plan& p, char* ws, cudaStream_t stream) {
                        : launch_roots_t<float>(p, ws, stream);
 }
 
-int launch_roots_batched(const BatchView& v, int64_t total_cta, int Q, int max_w,
+int launch_roots_batched(const BatchView& v, int64_t total_cta, int64_t dfs_cta, int Q, int max_w,
                          size_t max_stride, int precision, cudaStream_t stream) {
-    return precision ? launch_roots_batched_t<double>(v, total_cta, Q, max_w, max_stride, stream)
-                     : launch_roots_batched_t<float>(v, total_cta, Q, max_w, max_stride, stream);
+    return precision ? launch_roots_batched_t<double>(v, total_cta, dfs_cta, Q, max_w, max_stride,
+                                                      stream)
+                     : launch_roots_batched_t<float>(v, total_cta, dfs_cta, Q, max_w, max_stride,
+                                                     stream);
 }
 
 }  // namespace gbn
