@@ -138,10 +138,10 @@ int make_plan(int64_t n, int32_t m, const givensbn_opts* opts, Plan* p) {
     size_t off = 0;
     p->off_status = off;
     off = align_up(off + 256, 256);
-    p->off_colsum = off;
-    off = align_up(off + sizeof(double) * (size_t)p->panels * m, 256);
-    p->off_mu = off;
-    off = align_up(off + sizeof(double) * 32, 256);
+    p->off_colsum = off;  // per-panel column sums, then per-panel exponent maxima of |x|
+    off = align_up(off + sizeof(double) * 2 * (size_t)p->panels * m, 256);
+    p->off_mu = off;  // 32 means, then 32 column scale exponents
+    off = align_up(off + sizeof(double) * 64, 256);
     p->off_gram = off;
     off = align_up(off + sizeof(double) * (size_t)p->panels * (m * (m + 1) / 2), 256);
     p->off_gsum = off;

@@ -35,74 +35,164 @@ __device__ __forceinline__ void colsum_body(int b, const double* __restrict__ X,
                                             int rows_per, double* __restrict__ colsum, int panels,
                                             unsigned long long* chk) {
     __shared__ double red[256];
+    __shared__ int rede[256];
     const int64_t r0 = (int64_t)b * rows_per;
     const int64_t r1 = (r0 + rows_per < n) ? r0 + rows_per : n;
     const int per = blockDim.x / m;  // row lanes
     const int j = threadIdx.x % m;
     const int rl = threadIdx.x / m;
     double s = 0.0;
+    int emax = 0;  // the largest biased binary exponent of |x| (integer operations only)
     if (rl < per)
         for (int64_t t = r0 + rl; t < r1; t += per)
-            if (GBN_IN(chk, 101, t * m + j, n * m)) s += X[t * m + j];
-    if (GBN_IN(chk, 102, threadIdx.x, 256)) red[threadIdx.x] = (rl < per) ? s : 0.0;
+            if (GBN_IN(chk, 101, t * m + j, n * m)) {
+                const double x = X[t * m + j];
+                s += x;
+                emax = max(emax, (int)((__double_as_longlong(x) >> 52) & 0x7ff));
+            }
+    if (GBN_IN(chk, 102, threadIdx.x, 256)) {
+        red[threadIdx.x] = (rl < per) ? s : 0.0;
+        rede[threadIdx.x] = (rl < per) ? emax : 0;
+    }
     __syncthreads();
     if (threadIdx.x < m) {
         double acc = 0.0;
+        int em = 0;
         for (int l = 0; l < per; ++l)
-            if (GBN_IN(chk, 103, l * m + threadIdx.x, 256)) acc += red[l * m + threadIdx.x];
-        if (GBN_IN(chk, 104, (int64_t)b * m + threadIdx.x, (int64_t)panels * m))
+            if (GBN_IN(chk, 103, l * m + threadIdx.x, 256)) {
+                acc += red[l * m + threadIdx.x];
+                em = max(em, rede[l * m + threadIdx.x]);
+            }
+        if (GBN_IN(chk, 104, (int64_t)b * m + threadIdx.x, (int64_t)panels * m)) {
             colsum[(int64_t)b * m + threadIdx.x] = acc;
+            // the exponent maxima follow the sums, one integer per double slot
+            reinterpret_cast<long long*>(colsum)[(int64_t)(panels + b) * m + threadIdx.x] = em;
+        }
     }
 }
 
-// mu[j] = column mean of variable order[j] (zero when centring is off).
-// Threads split the panels of each column; four partial sums per thread.
+// mu[j] = column mean of variable order[j] (zero when centring is off), and
+// mu[32 + j] = that column's scale exponent: the unbiased binary exponent of its
+// largest |x| (0 for a zero column).  The Gram passes hold each centred column
+// times 2^-exponent (|y| < 4), so that their FP32-pair arithmetic stays inside
+// FP32's range for data of any scale.  Threads split the panels of each column.
 __device__ __forceinline__ void mean_body(const double* __restrict__ colsum, int panels, int m,
                                           int64_t n, int center, const Plan& plan,
                                           double* __restrict__ mu, unsigned long long* chk) {
     __shared__ double red[kRedThreads];
+    __shared__ int rede[kRedThreads];
     const int per = kRedThreads / m;  // threads per column
     const int j = threadIdx.x % m;
     const int l = threadIdx.x / m;
+    const long long* cexp = reinterpret_cast<const long long*>(colsum) + (int64_t)panels * m;
     double s = 0.0;
-    if (center && l < per) {
+    int em = 0;
+    if (l < per) {
         const int v = plan.order[j];
         for (int b = l; b < panels; b += per)
-            if (GBN_IN(chk, 131, (int64_t)b * m + v, (int64_t)panels * m))
-                s += colsum[(int64_t)b * m + v];
+            if (GBN_IN(chk, 131, (int64_t)b * m + v, (int64_t)panels * m)) {
+                if (center) s += colsum[(int64_t)b * m + v];
+                em = max(em, (int)cexp[(int64_t)b * m + v]);
+            }
     }
     red[threadIdx.x] = (l < per) ? s : 0.0;
+    rede[threadIdx.x] = (l < per) ? em : 0;
     __syncthreads();
     if (threadIdx.x < m) {
         double acc = 0.0;
-        for (int t = 0; t < per; ++t) acc += red[t * m + threadIdx.x];
+        int e = 0;
+        for (int t = 0; t < per; ++t) {
+            acc += red[t * m + threadIdx.x];
+            e = max(e, rede[t * m + threadIdx.x]);
+        }
         mu[threadIdx.x] = center ? acc / (double)n : 0.0;
+        mu[32 + threadIdx.x] = e > 0 ? (double)(e - 1023) : 0.0;
     }
 }
 
+// FP32-pair ("double-float") arithmetic for the panel Grams: a value is the
+// unevaluated sum hi + lo of two floats (47 significant bits here), products by
+// Dekker's method with FMA and sums by Knuth's TwoSum (Dekker, "A floating-point
+// technique for extending the available precision", Numer. Math. 18, 1971;
+// Knuth, TAOCP vol. 2, 4.2.2).  GB300 runs FP32 at 74 times its FP64 rate and
+// the Gram passes were bound by the FP64 pipe; here the centring subtraction
+// and the panel's final sums are the only FP64 operations.  The _rn intrinsics
+// keep the compiler from fusing the steps of the error-free transformations.
+//
+// y * 2^-s split into floats by integer operations (FP64 <-> FP32 conversions
+// also run on the slow FP64 pipe): hi = the sign, exponent and top 23 mantissa
+// bits; lo = the remaining 29 bits, normalised and truncated to 24.  Parts below
+// FP32's normal range (2^-126, relative to a column whose largest |x| is scaled
+// to [1, 2)) are dropped.
+__device__ __forceinline__ float2 df_split_int(double y, int s) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(y);
+    const int eb = (int)((b >> 52) & 0x7ff);
+    if (eb == 0) return make_float2(0.f, 0.f);  // zero (or subnormal)
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int E = eb - 1023 - s;  // unbiased exponent of y * 2^-s
+    const int ehi = E + 127;
+    if (ehi <= 0) return make_float2(0.f, 0.f);
+    const unsigned long long mant = b & 0x000FFFFFFFFFFFFFull;
+    const float hi = __uint_as_float(sign | ((unsigned)ehi << 23) | (unsigned)(mant >> 29));
+    const unsigned r = (unsigned)(mant & 0x1FFFFFFFull);  // value r * 2^(E - 52)
+    float lo = 0.f;
+    if (r) {
+        const int lz = __clz(r);  // >= 3
+        const int elo = E - 52 + (31 - lz) + 127;
+        if (elo > 0) lo = __uint_as_float(sign | ((unsigned)elo << 23) | ((r << (lz + 1)) >> 9));
+    }
+    return make_float2(hi, lo);
+}
+
+__device__ __forceinline__ float2 df_split(double x) {  // via conversions (a few per block)
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// (sh, sl) += a * b
+__device__ __forceinline__ void df_fma(float2 a, float2 b, float& sh, float& sl) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);  // the product's rounding error, exactly
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    const float t = __fadd_rn(sh, p);  // TwoSum(sh, p) = t + w exactly
+    const float v = __fsub_rn(t, sh);
+    const float w = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, v)), __fsub_rn(p, v));
+    const float lo = __fadd_rn(sl, __fadd_rn(e, w));
+    sh = __fadd_rn(t, lo);  // renormalise
+    sl = __fsub_rn(lo, __fsub_rn(sh, t));
+}
+
 // Partial Gram of one row panel: sum over its rows of y y^T (upper triangle,
-// packed by pairs i <= j), where y is the centred row in plan order, or for
-// pass 2 the row of Q1 = y R1^{-1} (Rinv = R1^{-1}, upper triangular).  Each
-// pair's thread adds the panel's even rows into one sum and the odd rows into
-// another (rows staged kPanelChunk at a time; the chunk size is even, so the
-// split, and the result, do not depend on it).
+// packed by pairs i <= j), where y is the centred row in plan order (centred in
+// FP64, scaled by the column's power of two and split into an FP32 pair), or for
+// pass 2 the row of Q1 = y R1^{-1} (Rinv = R1^{-1}, upper triangular; Q1's
+// entries are at most about 1), both accumulated in FP32 pairs.  Each pair's
+// thread adds the panel's even rows into one sum and the odd rows into another
+// (rows staged kPanelChunk at a time; the chunk size is even, so the split,
+// and the result, do not depend on it).  The panel's sums leave as FP64,
+// pass 1's scaled back exactly.
 __device__ __forceinline__ void gram_body(int blk, const double* __restrict__ X, int64_t n, int m,
                                           int rows_per, const double* __restrict__ mu_g, int panels,
                                           const double* __restrict__ Rinv, const Plan& plan,
                                           double* __restrict__ gram, unsigned long long* chk) {
     __shared__ double mu[32];
-    __shared__ double rows[kPanelChunk * kLd];
-    __shared__ double qrows[kPanelChunk * kLd];
-    __shared__ double ri[32 * kLd];
+    __shared__ int sx[32];  // column scale exponents: y' = y 2^-sx
+    __shared__ float2 rows[kPanelChunk * kLd];
+    __shared__ float2 qrows[kPanelChunk * kLd];
+    __shared__ float2 ri[32 * kLd];
     __shared__ int ord[32];  // the plan's column order (the plan may live in global memory)
     const int tid = threadIdx.x;
     if (tid < m) {
         mu[tid] = mu_g[tid];
+        sx[tid] = (int)mu_g[32 + tid];
         ord[tid] = plan.order[tid];
     }
-    if (Rinv)
+    __syncthreads();
+    if (Rinv)  // row i of R1^{-1} times 2^sx[i], so that y' Rinv' = y R1^{-1}
         for (int e = tid; e < m * m; e += blockDim.x)
-            if (GBN_IN(chk, 112, (e / m) * kLd + e % m, 32 * kLd)) ri[(e / m) * kLd + e % m] = Rinv[e];
+            if (GBN_IN(chk, 112, (e / m) * kLd + e % m, 32 * kLd))
+                ri[(e / m) * kLd + e % m] = df_split(ldexp(Rinv[e], sx[e / m]));
     const int npair = m * (m + 1) / 2;
     int pi = 0, pj = 0;
     if (tid < npair) {  // unpack pair index -> (i, j), i <= j
@@ -114,10 +204,10 @@ __device__ __forceinline__ void gram_body(int blk, const double* __restrict__ X,
         pi = i;
         pj = i + e;
     }
-    double acc0 = 0.0, acc1 = 0.0;
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
     const int64_t r0 = (int64_t)blk * rows_per;
     const int64_t rend = (r0 + rows_per < n) ? r0 + rows_per : n;
-    const double* src = Rinv ? qrows : rows;
+    const float2* src = Rinv ? qrows : rows;
     __syncthreads();
     for (int64_t c0 = r0; c0 < rend; c0 += kPanelChunk) {
         const int cnt = (rend - c0 < kPanelChunk) ? (int)(rend - c0) : kPanelChunk;
@@ -125,35 +215,32 @@ __device__ __forceinline__ void gram_body(int blk, const double* __restrict__ X,
             const int t = e / m, j = e % m;
             const int64_t xi = (c0 + t) * m + ord[j];
             if (GBN_IN(chk, 113, xi, n * m) && GBN_IN(chk, 114, t * kLd + j, kPanelChunk * kLd))
-                rows[t * kLd + j] = X[xi] - mu[j];
+                rows[t * kLd + j] = df_split_int(X[xi] - mu[j], sx[j]);
         }
         __syncthreads();
         if (Rinv) {  // Q1 rows: q[t][j] = sum_{i <= j} y[t][i] Rinv[i][j], one entry per thread
             for (int e = tid; e < cnt * m; e += blockDim.x) {
                 const int t = e / m, j = e % m;
-                double s0 = 0.0, s1 = 0.0;
-                int i = 0;
-                for (; i + 1 <= j; i += 2) {
-                    s0 = fma(rows[t * kLd + i], ri[i * kLd + j], s0);
-                    s1 = fma(rows[t * kLd + i + 1], ri[(i + 1) * kLd + j], s1);
-                }
-                if (i <= j) s0 = fma(rows[t * kLd + i], ri[i * kLd + j], s0);
-                qrows[t * kLd + j] = s0 + s1;
+                float sh = 0.f, sl = 0.f;
+                for (int i = 0; i <= j; ++i) df_fma(rows[t * kLd + i], ri[i * kLd + j], sh, sl);
+                qrows[t * kLd + j] = make_float2(sh, sl);
             }
             __syncthreads();
         }
         if (tid < npair) {
             int t = 0;
             for (; t + 1 < cnt; t += 2) {
-                acc0 = fma(src[t * kLd + pi], src[t * kLd + pj], acc0);
-                acc1 = fma(src[(t + 1) * kLd + pi], src[(t + 1) * kLd + pj], acc1);
+                df_fma(src[t * kLd + pi], src[t * kLd + pj], h0, l0);
+                df_fma(src[(t + 1) * kLd + pi], src[(t + 1) * kLd + pj], h1, l1);
             }
-            if (t < cnt) acc0 = fma(src[t * kLd + pi], src[t * kLd + pj], acc0);
+            if (t < cnt) df_fma(src[t * kLd + pi], src[t * kLd + pj], h0, l0);
         }
         __syncthreads();
     }
-    if (tid < npair && GBN_IN(chk, 115, (int64_t)blk * npair + tid, (int64_t)panels * npair))
-        gram[(int64_t)blk * npair + tid] = acc0 + acc1;
+    if (tid < npair && GBN_IN(chk, 115, (int64_t)blk * npair + tid, (int64_t)panels * npair)) {
+        const double g = ((double)h0 + (double)l0) + ((double)h1 + (double)l1);
+        gram[(int64_t)blk * npair + tid] = Rinv ? g : ldexp(g, sx[pi] + sx[pj]);
+    }
 }
 
 // Sum of the panel Grams for pairs [32 g, 32 g + 32): lane l of warp w adds
@@ -402,7 +489,6 @@ __global__ void colsum_kernel_b(const BatchView v) {
     int64_t local;
     const int d = batch_locate(v, v.panel_prefix, v.panel_pos, blockIdx.x, local);
     const Plan& p = v.plans[d];
-    if (!p.center) return;
     const R0Ptrs q = r0_ptrs(p, v.ws[d]);
     colsum_body((int)local, v.X[d], p.n, p.m, p.rows_per_panel, q.colsum, p.panels, q.chk);
 }
@@ -445,9 +531,8 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel_b(const BatchView v,
 
 int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream) {
     if (cudaMemsetAsync(ws + p.off_status, 0, 256, stream) != cudaSuccess) return GBN_ERR_CUDA;
-    if (p.center &&
-        launch_plain(colsum_kernel, dim3(p.panels), dim3(kColsumThreads), 0, stream, p, X, ws) !=
-            cudaSuccess)
+    if (launch_plain(colsum_kernel, dim3(p.panels), dim3(kColsumThreads), 0, stream, p, X, ws) !=
+        cudaSuccess)
         return GBN_ERR_CUDA;
     const unsigned groups = (unsigned)((p.m * (p.m + 1) / 2 + 31) / 32);
     const cudaError_t e[] = {
