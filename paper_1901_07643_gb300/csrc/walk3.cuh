@@ -50,8 +50,10 @@
 //     consumers replay the previous one.
 #pragma once
 
+#include <mutex>
 #include <type_traits>
 #include <utility>
+#include <vector>
 
 #include "gbn_internal.cuh"
 
@@ -1140,6 +1142,49 @@ constexpr bool pair_walk_compiled() {
     return std::is_same<T, float>::value && !COV && SmemP<Q>::bytes <= kPairMaxSmem;
 }
 
+// ------------------------------------------------- resident blocks (cached)
+// SMs x resident blocks per SM of a persistent kernel at a launch shape, found
+// once per (kernel, device, threads, shared memory): the occupancy query costs
+// more host time than a launch, and a small call's kernels are short enough for
+// host time to show.  The first query for a kernel on a device also sets its
+// dynamic shared-memory limit to smem_max (at least any launch's).
+struct ResidentEntry {
+    const void* fn;
+    int dev, threads;
+    size_t smem;
+    int blocks;
+};
+
+template <typename K>
+int resident_blocks(K* kernel, int threads, size_t smem, size_t smem_max, int* blocks) {
+    static std::mutex mu;
+    static std::vector<ResidentEntry> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return GBN_ERR_CUDA;
+    const void* fn = reinterpret_cast<const void*>(kernel);
+    std::lock_guard<std::mutex> lock(mu);
+    bool limit_set = false;
+    for (const ResidentEntry& e : cache) {
+        if (e.fn != fn || e.dev != dev) continue;
+        limit_set = true;
+        if (e.threads == threads && e.smem == smem) {
+            *blocks = e.blocks;
+            return GBN_OK;
+        }
+    }
+    int sms = 0, per_sm = 0;
+    if ((!limit_set && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem_max) != cudaSuccess) ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+            cudaSuccess)
+        return GBN_ERR_CUDA;
+    if (per_sm < 1) return GBN_ERR_CUDA;
+    cache.push_back(ResidentEntry{fn, dev, threads, smem, sms * per_sm});
+    *blocks = sms * per_sm;
+    return GBN_OK;
+}
+
 // ---------------------------------------------------------------- ring walk
 // A persistent form of the FP32 walk.  A unit is one roots CTA's 32
 // sub-walks (PAIR: two neighbouring ones, as in the paired walk); block b takes
@@ -1236,17 +1281,10 @@ template <int Q, bool PAIR>
 int launch_walk_ring(const WalkArgs<float>& a, int64_t n_units, cudaStream_t stream) {
     const size_t smem = RingSmem<Q, PAIR>::bytes;
     const int threads = ring_threads<Q, PAIR>();
-    if (cudaFuncSetAttribute(walk_ring_kernel<Q, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return GBN_ERR_CUDA;
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_ring_kernel<Q, PAIR>, threads,
-                                                      smem) != cudaSuccess)
-        return GBN_ERR_CUDA;
-    if (per_sm < 1) return GBN_ERR_CUDA;
-    const int64_t blocks = std::min<int64_t>(n_units, (int64_t)sms * per_sm);
+    int resident = 0;
+    const int rc = resident_blocks(walk_ring_kernel<Q, PAIR>, threads, smem, smem, &resident);
+    if (rc != GBN_OK) return rc;
+    const int64_t blocks = std::min<int64_t>(n_units, (int64_t)resident);
     return launch_rc(launch_plain(walk_ring_kernel<Q, PAIR>, dim3((unsigned)blocks), dim3(threads),
                                   smem, stream, a, n_units));
 }
