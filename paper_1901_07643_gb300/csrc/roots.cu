@@ -476,7 +476,8 @@ __device__ __forceinline__ void write_leaf_q(const T (&M)[RT], T C, const Plan& 
 
 // Stage leaf ell's record in shared memory, stg[8 e + (ell & 7) + skew(e)]; after
 // the eighth leaf of a group (the enumeration runs ell = 31 down to 0) write
-// the group out as 8-float runs, one full 32-byte sector per record element.
+// the group out as 8-element runs, one full 32-byte sector per record element
+// (FP32: two 16-byte stores).
 template <typename T, int Q, int RT>
 __device__ __forceinline__ void stage_leaf_q(const T (&M)[RT], T C, const Plan& p, int lane,
                                              unsigned carried_mask, int ell, T* stg, T* rec,
@@ -502,9 +503,22 @@ __device__ __forceinline__ void stage_leaf_q(const T (&M)[RT], T C, const Plan& 
     if (j == 0) {  // the group ell .. ell + 7 is complete
         __syncwarp();
         const int R = (int)(p.leaf_stride / 32);
-        for (int idx = lane; idx < R * 8; idx += 32) {
-            const size_t ix = (size_t)(idx >> 3) * 32 + ell + (idx & 7);
-            if (GBN_IN(chk, 227, ix, p.leaf_stride)) rec[ix] = stg[idx + stage_skew<Q>(idx >> 3)];
+        if constexpr (std::is_same<T, float>::value) {
+            // four leaves of one element per lane: one 16-byte store (ell is a
+            // multiple of 8 here and records start 128-byte aligned)
+            for (int u = lane; u < R * 2; u += 32) {
+                const int e = u >> 1, h4 = (u & 1) * 4;
+                const float* src = stg + 8 * e + h4 + stage_skew<Q>(e);
+                const size_t ix = (size_t)e * 32 + ell + h4;
+                if (GBN_IN(chk, 227, ix + 3, p.leaf_stride))
+                    *reinterpret_cast<float4*>(rec + ix) = make_float4(src[0], src[1], src[2], src[3]);
+            }
+        } else {
+            for (int idx = lane; idx < R * 8; idx += 32) {
+                const size_t ix = (size_t)(idx >> 3) * 32 + ell + (idx & 7);
+                if (GBN_IN(chk, 227, ix, p.leaf_stride))
+                    rec[ix] = stg[idx + stage_skew<Q>(idx >> 3)];
+            }
         }
         __syncwarp();
     }
