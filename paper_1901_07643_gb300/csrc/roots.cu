@@ -83,6 +83,23 @@ __device__ __forceinline__ int var_of_lane(const Plan& p, int lane) {
     return lane < kw ? lane + p.W : (lane < p.k ? p.W - 1 - (lane - kw) : lane);
 }
 
+// Compact leaf records: the fixed variables above the lowest W that are in the
+// CTA's front set (the same for all its leaves) are never read by the walk, so
+// they get no slot.  Slot of fixed variable lane `lane` in a leaf whose carried
+// mask is `carried`: the lowest W variables keep slots 0 .. W-1; a variable
+// above them outside the front set takes slot W + the number of such variables
+// below it (the order in which the walk's items take them).
+__device__ __forceinline__ int rec_slot(const Plan& p, int lane, unsigned carried) {
+    const int kw = p.k - p.W;
+    return lane < kw ? p.W + __popc(carried & ((1u << lane) - 1u)) : var_of_lane(p, lane);
+}
+// Record elements (per lane) in use: the L block and W + nu slots of Q + 1.
+__device__ __forceinline__ int rec_rows(const Plan& p, unsigned carried) {
+    const int kw = p.k - p.W;
+    const int nu = __popc(carried & ((1u << kw) - 1u));
+    return p.Q * (p.Q + 1) / 2 + (p.W + nu) * (p.Q + 1);
+}
+
 // ------------------------------------------------------------- top levels
 
 // A node in shared memory: live rows r0 .. r0 + rows - 1 of S (row r of the
@@ -317,7 +334,7 @@ __device__ __forceinline__ void write_leaf(const T (&M)[kDfsRows], T C, const Pl
             }
         });
     } else if (lane < k && ((carried_mask >> lane) & 1u)) {  // fixed variable in B
-        const size_t b0 = (size_t)(LQ + var_of_lane(p, lane) * (Q + 1)) * 32 + ell;
+        const size_t b0 = (size_t)(LQ + rec_slot(p, lane, carried_mask) * (Q + 1)) * 32 + ell;
         sfor(std::make_integer_sequence<int, kDfsRows>{}, [&](auto rc) {
             constexpr int r = decltype(rc)::value;
             if (r < Q) {
@@ -450,30 +467,6 @@ __device__ __forceinline__ void load_n(const T* st, T (&M)[RT], T& C, unsigned& 
     carried = *mask_of(const_cast<T*>(st), rows);
 }
 
-template <typename T, int Q, int RT>
-__device__ __forceinline__ void write_leaf_q(const T (&M)[RT], T C, const Plan& p, int lane,
-                                             unsigned carried_mask, int ell, T* rec,
-                                             unsigned long long* chk) {
-    constexpr int LQ = Q * (Q + 1) / 2;
-    const int k = p.k;
-    if (lane >= k && lane < p.m) {  // L column i: rows 0 .. i of the L block
-        const int i = lane - k;
-        const size_t b0 = (size_t)(i * (i + 1) / 2) * 32 + ell;
-        sfor(std::make_integer_sequence<int, Q>{}, [&](auto rc) {
-            constexpr int r = decltype(rc)::value;
-            if (r <= i && GBN_IN(chk, 221, b0 + (size_t)r * 32, p.leaf_stride))
-                rec[b0 + (size_t)r * 32] = M[r];
-        });
-    } else if (lane < k && ((carried_mask >> lane) & 1u)) {  // fixed variable in B
-        const size_t b0 = (size_t)(LQ + var_of_lane(p, lane) * (Q + 1)) * 32 + ell;
-        sfor(std::make_integer_sequence<int, Q>{}, [&](auto rc) {
-            constexpr int r = decltype(rc)::value;
-            if (GBN_IN(chk, 224, b0 + (size_t)r * 32, p.leaf_stride)) rec[b0 + (size_t)r * 32] = M[r];
-        });
-        if (GBN_IN(chk, 225, b0 + (size_t)Q * 32, p.leaf_stride)) rec[b0 + (size_t)Q * 32] = C;
-    }
-}
-
 // Stage leaf ell's record in shared memory, stg[8 e + (ell & 7) + skew(e)]; after
 // the eighth leaf of a group (the enumeration runs ell = 31 down to 0) write
 // the group out as 8-element runs, one full 32-byte sector per record element
@@ -492,7 +485,7 @@ __device__ __forceinline__ void stage_leaf_q(const T (&M)[RT], T C, const Plan& 
             if (r <= i) sb[8 * r] = M[r];
         });
     } else if (lane < k && ((carried_mask >> lane) & 1u)) {  // fixed variable in B
-        const int v = var_of_lane(p, lane);
+        const int v = rec_slot(p, lane, carried_mask);
         T* sb = stg + 8 * (LQ + v * (Q + 1)) + j + 1 + v;
         sfor(std::make_integer_sequence<int, Q>{}, [&](auto rc) {
             constexpr int r = decltype(rc)::value;
@@ -502,7 +495,7 @@ __device__ __forceinline__ void stage_leaf_q(const T (&M)[RT], T C, const Plan& 
     }
     if (j == 0) {  // the group ell .. ell + 7 is complete
         __syncwarp();
-        const int R = (int)(p.leaf_stride / 32);
+        const int R = rec_rows(p, carried_mask);  // the record's elements in use
         if constexpr (std::is_same<T, float>::value) {
             // four leaves of one element per lane: one 16-byte store (ell is a
             // multiple of 8 here and records start 128-byte aligned)

@@ -923,10 +923,11 @@ __device__ __forceinline__ int consume_pair(const WalkArgs<float>& a, const floa
             sh = a.k;
             slot = ((size_t)(a.k + j) << (a.m - 1)) + ((pc << 6) | ((uint64_t)pl << 1));
         } else {  // a fixed variable v outside the front sets
-            int v;
+            int v, rs;  // rs: the variable's slot in the (compact) leaf record
             bool on = true;
-            if (it < Q + nu) {  // above 5
+            if (it < Q + nu) {  // above 5: record 0 (variable 5 outside F) holds it one slot up
                 v = 6 + nth_zero_bit(pc, it - Q);
+                rs = 6 - (pl >> 4) + (it - Q);
             } else if (it < Q + nu + 3) {  // 1..5, 16 pair lanes each (bit v-1 of pl clear)
                 const int j = it - Q - nu;
                 const int uu = lane >> 4, sub = lane & 15;
@@ -936,12 +937,14 @@ __device__ __forceinline__ int consume_pair(const WalkArgs<float>& a, const floa
                 pl = (sub & ((1 << b) - 1)) | ((sub >> b) << (b + 1));
                 if (!on) v = 1;
                 on_xy = on ? 1u : 0u;
+                rs = v;
             } else {  // variable 0: a child of x only
                 v = 0;
+                rs = 0;
                 on_xy = 0u;
                 on_x = 1u;
             }
-            const size_t b0 = (size_t)32 * (LQ + v * (Q + 1));
+            const size_t b0 = (size_t)32 * (LQ + rs * (Q + 1));
 #pragma unroll
             for (int e = 0; e < Q; ++e) z[e] = ld2(b0 + (size_t)e * 32, pl, on, 331);
             cres = ld2(b0 + (size_t)Q * 32, pl, on, 331);
@@ -996,9 +999,10 @@ __device__ __forceinline__ int consume(const WalkArgs<T>& a, const T* __restrict
             base = reinterpret_cast<OutT<T, COV>*>(a.out) + ((size_t)(a.k + j) << (a.m - 1)) +
                    (Fhi | (uint64_t)lane);
         } else {  // fixed variable v outside the front set
-            int v;
+            int v, rs;  // rs: the variable's slot in the (compact) leaf record
             if (it < Q + nu) {
                 v = a.W + nth_zero_bit(cta, it - Q);
+                rs = a.W + (it - Q);
                 on = lane < a.lanes;
             } else {
                 const int j = it - Q - nu;
@@ -1007,8 +1011,9 @@ __device__ __forceinline__ int consume(const WalkArgs<T>& a, const T* __restrict
                 on = v < a.W;
                 ell = on ? ((sub & ((1 << v) - 1)) | ((sub >> v) << (v + 1))) : 0;
                 if (!on) v = 0;
+                rs = v;
             }
-            const size_t b0 = (size_t)32 * (LQ + v * (Q + 1));
+            const size_t b0 = (size_t)32 * (LQ + rs * (Q + 1));
 #pragma unroll
             for (int e = 0; e < Q; ++e) {
                 const size_t ix = b0 + e * 32 + ell;
@@ -1116,12 +1121,19 @@ __device__ __forceinline__ void walk_pair_body(const WalkArgs<float>& a, uint64_
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + S::off_bar);
     for (int c = threadIdx.x; c < S::chunks; c += blockDim.x) mbar_init(&full[c], 2);
-    prefetch_l2(a.leaves + (size_t)(2 * pc) * a.leaf_stride, 2 * a.leaf_stride * sizeof(float),
-                threadIdx.x, blockDim.x);
-    __syncthreads();
     uint64_t gpc = pc;
+    if constexpr (GEN) gpc += (uint64_t)a.cta0 >> 1;
+    {  // the elements in use of the two compact records (CTA 2 gpc + h: nu_h slots above 5)
+        constexpr int LQ = Q * (Q + 1) / 2;
+        const int nu0 = (a.k - 5) - __popcll(2 * gpc);
+        const float* r0 = a.leaves + (size_t)(2 * pc) * a.leaf_stride;
+        prefetch_l2(r0, (size_t)(LQ + (5 + nu0) * (Q + 1)) * 32 * sizeof(float), threadIdx.x,
+                    blockDim.x);
+        prefetch_l2(r0 + a.leaf_stride, (size_t)(LQ + (4 + nu0) * (Q + 1)) * 32 * sizeof(float),
+                    threadIdx.x, blockDim.x);
+    }
+    __syncthreads();
     if constexpr (GEN) {
-        gpc += (uint64_t)a.cta0 >> 1;
         if (__popcll(gpc) > a.kmax) return;  // every family here has too many parents
     }
     const float* rec0 = a.leaves + (size_t)(2 * pc) * a.leaf_stride;
