@@ -47,6 +47,7 @@ struct BatchLayout {
     size_t off_cta_prefix = 0, off_panel_prefix = 0, off_dataset_of = 0, off_plans = 0,
            off_X = 0, off_ws = 0, off_out = 0, off_args = 0;
     size_t off_panel_pos = 0, off_cta_pos = 0;  // position maps, filled on the device
+    size_t off_pass2 = 0;                       // pass-2 panel prefix, filled on the device
 };
 
 int plan_batch(const int64_t* ns, const int32_t* ms, int32_t B, const givensbn_opts* opts,
@@ -133,6 +134,8 @@ int plan_batch(const int64_t* ns, const int32_t* ms, int32_t B, const givensbn_o
     off = up256(off + sizeof(int32_t) * (size_t)L->total_panels);
     L->off_cta_pos = off;
     off = up256(off + sizeof(int32_t) * (size_t)(L->total_cta > 0 ? L->total_cta : 1));
+    L->off_pass2 = off;
+    off = up256(off + sizeof(int64_t) * (size_t)(B + 1));
     L->ws_off.resize(B);
     for (int b = 0; b < B; ++b) {
         L->ws_off[b] = off;
@@ -242,6 +245,7 @@ extern "C" int score_all_families_batched(const double* const* Xs, const int64_t
     v.dataset_of = reinterpret_cast<const int32_t*>(base + L.off_dataset_of);
     v.panel_pos = reinterpret_cast<int32_t*>(base + L.off_panel_pos);
     v.cta_pos = reinterpret_cast<int32_t*>(base + L.off_cta_pos);
+    v.pass2_prefix = reinterpret_cast<int64_t*>(base + L.off_pass2);
     v.plans = reinterpret_cast<const Plan*>(base + L.off_plans);
     v.X = reinterpret_cast<const double* const*>(base + L.off_X);
     v.ws = reinterpret_cast<char* const*>(base + L.off_ws);
@@ -404,6 +408,7 @@ extern "C" int score_all_families_backward_batched(const double* const* Xs, cons
     v.dataset_of = reinterpret_cast<const int32_t*>(base + L.off_dataset_of);
     v.panel_pos = reinterpret_cast<int32_t*>(base + L.off_panel_pos);
     v.cta_pos = reinterpret_cast<int32_t*>(base + L.off_cta_pos);
+    v.pass2_prefix = reinterpret_cast<int64_t*>(base + L.off_pass2);
     v.plans = reinterpret_cast<const Plan*>(base + L.off_plans);
     v.X = reinterpret_cast<const double* const*>(base + L.off_X);
     v.ws = reinterpret_cast<char* const*>(base + L.off_ws);

@@ -168,6 +168,8 @@ struct BatchView {
     const int32_t* dataset_of = nullptr;    // launch position -> dataset index
     int32_t* panel_pos = nullptr;           // global row panel -> launch position
     int32_t* cta_pos = nullptr;             // global sub-walk CTA -> launch position
+    int64_t* pass2_prefix = nullptr;        // B+1: row panels of the datasets that need
+                                            // CholeskyQR's second pass (filled on the device)
     const Plan* plans = nullptr;
     const double* const* X = nullptr;
     char* const* ws = nullptr;              // per-dataset workspace region

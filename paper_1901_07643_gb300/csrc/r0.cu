@@ -15,6 +15,8 @@
 // variables in), so R0 is the R factor of Xc[:, order].
 #include <math.h>
 
+#include <algorithm>
+
 #include "gbn_internal.cuh"
 
 namespace gbn {
@@ -485,12 +487,18 @@ __global__ void status_clear_kernel_b(const BatchView v) {
     int* st = reinterpret_cast<int*>(v.ws[d] + v.plans[d].off_status);
     for (int i = threadIdx.x; i < 64; i += blockDim.x) st[i] = 0;
 }
-__global__ void colsum_kernel_b(const BatchView v) {
-    int64_t local;
-    const int d = batch_locate(v, v.panel_prefix, v.panel_pos, blockIdx.x, local);
-    const Plan& p = v.plans[d];
-    const R0Ptrs q = r0_ptrs(p, v.ws[d]);
-    colsum_body((int)local, v.X[d], p.n, p.m, p.rows_per_panel, q.colsum, p.panels, q.chk);
+// The batched column sums loop over the batch's row panels on a few blocks per
+// SM (grid-stride): one small block per panel, about 20,000 for the bootstrap
+// batch, cost more to launch than the panels' work (51 -> 43 us).
+__global__ void colsum_kernel_b(const BatchView v, int64_t P) {
+    for (int64_t g = blockIdx.x; g < P; g += gridDim.x) {
+        int64_t local;
+        const int d = batch_locate(v, v.panel_prefix, v.panel_pos, g, local);
+        const Plan& p = v.plans[d];
+        const R0Ptrs q = r0_ptrs(p, v.ws[d]);
+        colsum_body((int)local, v.X[d], p.n, p.m, p.rows_per_panel, q.colsum, p.panels, q.chk);
+        __syncthreads();  // the shared reduction buffers are reused by the next panel
+    }
 }
 __global__ void __launch_bounds__(kRedThreads) mean_kernel_b(const BatchView v) {
     const int d = blockIdx.x;
@@ -498,12 +506,68 @@ __global__ void __launch_bounds__(kRedThreads) mean_kernel_b(const BatchView v) 
     const R0Ptrs q = r0_ptrs(p, v.ws[d]);
     mean_body(q.colsum, p.panels, p.m, p.n, p.center, p, q.mu, q.chk);
 }
+// The row panels of the datasets that need the second CholeskyQR pass, as a
+// prefix over launch positions (datasets that took one pass count none): one
+// block scans the one-pass flags after the first pass, so that the second
+// pass's Gram blocks map onto that work alone, and the rest return after one
+// load instead of each looking its dataset and flag up (the bootstrap batch's
+// datasets are mostly well conditioned).
+__global__ void __launch_bounds__(1024) pass2_prefix_kernel_b(const BatchView v) {
+    __shared__ int64_t part[1024];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) {
+        carry = 0;
+        v.pass2_prefix[0] = 0;
+    }
+    __syncthreads();
+    for (int b0 = 0; b0 < v.B; b0 += blockDim.x) {
+        const int l = b0 + (int)threadIdx.x;
+        int64_t c = 0;
+        if (l < v.B) {
+            const int d = v.dataset_of[l];
+            const Plan& p = v.plans[d];
+            const R0Ptrs q = r0_ptrs(p, v.ws[d]);
+            c = *q.onepass ? 0 : p.panels;
+        }
+        part[threadIdx.x] = c;
+        __syncthreads();
+        for (unsigned o = 1; o < blockDim.x; o <<= 1) {  // inclusive scan
+            const int64_t t = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+            __syncthreads();
+            part[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (l < v.B) v.pass2_prefix[l + 1] = carry + part[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += part[threadIdx.x];
+        __syncthreads();
+    }
+}
+// Pass 1: one block per row panel of the batch.  Pass 2: block bx is panel bx of
+// the pass-2 prefix (a binary search for its launch position), if there is one.
+// (A grid-stride form of either pass, a few blocks per SM looping over the
+// panels, measured slower: the Gram is bound by its work, not by its launch.)
 __global__ void gram_kernel_b(const BatchView v, int pass) {
     int64_t local;
-    const int d = batch_locate(v, v.panel_prefix, v.panel_pos, blockIdx.x, local);
+    int d;
+    if (pass) {
+        const int64_t bx = blockIdx.x;
+        if (bx >= v.pass2_prefix[v.B]) return;
+        int lo = 0, hi = v.B;  // pass2_prefix[lo] <= bx < pass2_prefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (v.pass2_prefix[mid] <= bx)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        local = bx - v.pass2_prefix[lo];
+        d = v.dataset_of[lo];
+    } else {
+        d = batch_locate(v, v.panel_prefix, v.panel_pos, blockIdx.x, local);
+    }
     const Plan& p = v.plans[d];
     const R0Ptrs q = r0_ptrs(p, v.ws[d]);
-    if (pass && *q.onepass) return;
     gram_body((int)local, v.X[d], p.n, p.m, p.rows_per_panel, q.mu, p.panels,
               pass ? q.r1inv : nullptr, p, q.gram, q.chk);
 }
@@ -548,18 +612,27 @@ int launch_r0(const Plan& p, const double* X, char* ws, cudaStream_t stream) {
     return GBN_OK;
 }
 
+constexpr int kColsumBlocksPerSm = 16;
+
 int launch_r0_batched(const BatchView& v, int64_t total_panels, int max_m, cudaStream_t stream) {
-    const unsigned B = (unsigned)v.B, P = (unsigned)total_panels;
+    const unsigned B = (unsigned)v.B;
+    const int64_t P = total_panels;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GBN_ERR_CUDA;
+    const unsigned g_colsum = (unsigned)std::min<int64_t>(P, (int64_t)sms * kColsumBlocksPerSm);
     const dim3 sum_grid((unsigned)((max_m * (max_m + 1) / 2 + 31) / 32), B);
     const cudaError_t e[] = {
         launch_plain(batch_pos_kernel, dim3(B, 2), dim3(256), 0, stream, v),
         launch_plain(status_clear_kernel_b, dim3(B), dim3(64), 0, stream, v),
-        launch_plain(colsum_kernel_b, dim3(P), dim3(kColsumThreads), 0, stream, v),
+        launch_plain(colsum_kernel_b, dim3(g_colsum), dim3(kColsumThreads), 0, stream, v, P),
         launch_plain(mean_kernel_b, dim3(B), dim3(kRedThreads), 0, stream, v),
-        launch_plain(gram_kernel_b, dim3(P), dim3(gram_threads(max_m)), 0, stream, v, 0),
+        launch_plain(gram_kernel_b, dim3((unsigned)P), dim3(gram_threads(max_m)), 0, stream, v, 0),
         launch_plain(gram_sum_kernel_b, sum_grid, dim3(kRedThreads), 0, stream, v, 0),
         launch_plain(chol_kernel_b, dim3(B), dim3(kCholThreads), 0, stream, v, 0),
-        launch_plain(gram_kernel_b, dim3(P), dim3(gram_threads(max_m)), 0, stream, v, 1),
+        launch_plain(pass2_prefix_kernel_b, dim3(1), dim3(1024), 0, stream, v),
+        launch_plain(gram_kernel_b, dim3((unsigned)P), dim3(gram_threads(max_m)), 0, stream, v, 1),
         launch_plain(gram_sum_kernel_b, sum_grid, dim3(kRedThreads), 0, stream, v, 1),
         launch_plain(chol_kernel_b, dim3(B), dim3(kCholThreads), 0, stream, v, 1)};
     for (cudaError_t x : e)
