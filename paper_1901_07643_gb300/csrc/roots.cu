@@ -622,14 +622,15 @@ __host__ __device__ __forceinline__ size_t leaf_warp_elems(const Plan& p) {
                                               : warp_smem_elems(p.Q, p.W, p.leaf_stride);
 }
 
-// The FP32 form (REG) gives a walk CTA two warps: half 0 / 1 takes the
-// exclude / include branch of the first leaf level and the 16 leaves below
-// it, so that twice as many warps share the chains of rotations.  The FP64
-// form (shared-memory stack) enumerates all 32 leaves in one warp.
+// The FP32 form (REG) gives a walk CTA four warps: quarter qd takes the
+// choices of bits 1 and 0 of qd (1: join F) at the first two leaf levels and
+// enumerates the 8 leaves below them, so that four times as many warps share
+// the chains of rotations and each keeps three levels' nodes in registers.
+// The FP64 form (shared-memory stack) enumerates all 32 leaves in one warp.
 template <typename T, int Q, bool REG>
 __device__ __forceinline__ void leaves_w5(const T* __restrict__ top, const Plan& p,
                                           T* __restrict__ leaves, unsigned long long* chk,
-                                          uint64_t cta, T* stack, int half = -1) {
+                                          uint64_t cta, T* stack, int qd = -1) {
     constexpr int RT = Q + 5;
     const int lane = threadIdx.x & 31;
     T M[RT];
@@ -639,13 +640,20 @@ __device__ __forceinline__ void leaves_w5(const T* __restrict__ top, const Plan&
     if constexpr (REG) {  // staging at the start of the warp's shared memory
         T* rec = leaves + (size_t)cta * p.leaf_stride;
         const int topk = p.k - 5;
-        if (half) {
+        const int b0 = (qd >> 1) & 1, b1 = qd & 1;
+        if (b0) {
             include_n<T, RT, RT>(M);
         } else {
             carried |= 1u << topk;
             exclude_r<T, RT, RT>(M, C, topk, (carried >> lane) & 1u);
         }
-        Dfs5R<T, Q, 1>::run(M, C, carried, lane, topk, half << 4, stack, p, rec, chk);
+        if (b1) {
+            include_n<T, RT, RT - 1>(M);
+        } else {
+            carried |= 1u << (topk + 1);
+            exclude_r<T, RT, RT - 1>(M, C, topk + 1, (carried >> lane) & 1u);
+        }
+        Dfs5R<T, Q, 2>::run(M, C, carried, lane, topk, (b0 << 4) | (b1 << 3), stack, p, rec, chk);
     } else
         Dfs5<T, Q, 0>::run(M, C, carried, lane, p.k - 5, 0, stack, p,
                            leaves + (size_t)cta * p.leaf_stride, chk);
@@ -694,13 +702,13 @@ __global__ void __launch_bounds__(32 * kTopDfsWarps) roots_top_dfs_kernel(const 
 // with the stack in registers, FP64 in shared memory), or 0 for the generic
 // one; each instance gets the registers its own Q needs.
 template <typename T, int QF>
-__global__ void __launch_bounds__(32 * kDfsWarps, (std::is_same<T, float>::value && QF > 0) ? 7 : 1)
+__global__ void __launch_bounds__(32 * kDfsWarps, (std::is_same<T, float>::value && QF > 0) ? 8 : 1)
     roots_leaves_kernel(const Plan p, char* ws) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     grid_dep_wait();
     const int warp = threadIdx.x >> 5;
     constexpr bool kReg = std::is_same<T, float>::value && QF > 0;
-    constexpr int kWarpsPerCta = kReg ? 2 : 1;
+    constexpr int kWarpsPerCta = kReg ? 4 : 1;
     const uint64_t gw = (uint64_t)blockIdx.x * kDfsWarps + warp;
     const uint64_t cta = gw / kWarpsPerCta;
     if (cta >= (uint64_t)p.n_cta) return;
@@ -711,7 +719,7 @@ __global__ void __launch_bounds__(32 * kDfsWarps, (std::is_same<T, float>::value
     unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
     if constexpr (QF > 0)
         leaves_w5<T, QF, kReg>(top_nodes<T>(p, ws), p, leaves, chk, cta, stack,
-                               kReg ? (int)(gw & 1) : -1);
+                               kReg ? (int)(gw & 3) : -1);
     else
         leaves_body<T>(top_nodes<T>(p, ws), p, leaves, chk, cta, stack);
 }
@@ -772,7 +780,7 @@ int launch_leaves_q(const Plan& p, char* ws, size_t smem, cudaStream_t stream) {
     if (cudaFuncSetAttribute(roots_leaves_kernel<T, QF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return GBN_ERR_CUDA;
-    const int warps_per_cta = (std::is_same<T, float>::value && QF > 0) ? 2 : 1;
+    const int warps_per_cta = (std::is_same<T, float>::value && QF > 0) ? 4 : 1;
     const unsigned nb = (unsigned)((p.n_cta * warps_per_cta + kDfsWarps - 1) / kDfsWarps);
     if (launch_dep(roots_leaves_kernel<T, QF>, dim3(nb), dim3(32 * kDfsWarps), smem, stream, p, ws) !=
         cudaSuccess)
@@ -816,16 +824,16 @@ int launch_roots_t(const Plan& p, char* ws, cudaStream_t stream) {
     return rc;
 }
 
-// A batch whose datasets all have W = 5 (FP32, a compiled Q): the two-warp
+// A batch whose datasets all have W = 5 (FP32, a compiled Q): the four-warp
 // register-stack leaf enumeration of the single-dataset kernel, warps finding
 // their dataset through the prefix of walk CTAs.
 template <typename T, int QF>
-__global__ void __launch_bounds__(32 * kDfsWarps, 7)
+__global__ void __launch_bounds__(32 * kDfsWarps, 8)
     roots_leaves_kernel_bq(const BatchView v, size_t max_stride) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * kDfsWarps + warp;
-    const int64_t g = gw >> 1;
+    const int64_t g = gw >> 2;
     if (g >= v.cta_prefix[v.B]) return;
     int64_t local;
     const int d = batch_locate(v, v.cta_prefix, v.cta_pos, g, local);
@@ -834,7 +842,7 @@ __global__ void __launch_bounds__(32 * kDfsWarps, 7)
     T* stg = reinterpret_cast<T*>(smem_raw) + warp * stage_elems(max_stride);
     unsigned long long* chk = reinterpret_cast<unsigned long long*>(ws + p.off_status + kCheckOffset);
     leaves_w5<T, QF, true>(top_nodes<T>(p, ws), p, reinterpret_cast<T*>(ws + p.off_leaves), chk,
-                           (uint64_t)local, stg, (int)(gw & 1));
+                           (uint64_t)local, stg, (int)(gw & 3));
 }
 
 template <typename T, int QF>
@@ -844,7 +852,7 @@ int launch_leaves_bq(const BatchView& v, int64_t total_cta, size_t max_stride,
     if (cudaFuncSetAttribute(roots_leaves_kernel_bq<T, QF>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return GBN_ERR_CUDA;
-    const unsigned nb = (unsigned)((2 * total_cta + kDfsWarps - 1) / kDfsWarps);
+    const unsigned nb = (unsigned)((4 * total_cta + kDfsWarps - 1) / kDfsWarps);
     return launch_rc(launch_plain(roots_leaves_kernel_bq<T, QF>, dim3(nb), dim3(32 * kDfsWarps),
                                   smem, stream, v, max_stride));
 }
